@@ -1,0 +1,675 @@
+/*
+ * Oracle: the moment-chain LBM for non-linear solids, plain FP64 C.
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).  It follows Algorithm 1 of the
+ * paper in its printed order, one whole-lattice pass per block:
+ *   1. moments, equilibrium, forcing, collision, streaming   (Alg. 1, Sect. 3.2)
+ *   2. bounce-back / anti-bounce-back boundaries             (Eq. bbcon, abbcon)
+ *   3. displacement gradient and stresses                    (Eq. defgrad, Sect. 4)
+ *   4. source term, moments, trapezoidal displacement update (Eq. source, Sect. 3.2)
+ *
+ * Readings where the paper is silent, garbled or inconsistent (each is listed
+ * in the design notes of the repository):
+ *   R1  collision uses the algorithm's form
+ *       f - (dt/tau)(f - feq) + (1 - dt/(2 tau)) psi dt   (Eq. for the collision
+ *       step in Sect. 2 has a misplaced bracket), with tau given in units of dt.
+ *   R2  the trapezoidal update carries the time step:
+ *       u(t+dt) = u(t) + dt/(2 rho0) (j(t+dt) + j(t)).
+ *   R3  Pi(H) = -mu (H + H^T + tr(H) I): the constitutive momentum flux implied by
+ *       the third line of the moment chain with Q = c_s^2 (j d + j d + j d),
+ *       j = rho0 du/dt and c_s^2 rho0 = mu.
+ *   R4  Lame constants are plane strain: mu = E/(2(1+nu)),
+ *       lam = E nu/((1+nu)(1-2 nu)) (the only choice that reproduces the CFL
+ *       bounds nu <= 1/4 and nu <= 5/11 quoted in Sect. 3.2).
+ *   R5  finite differences are applied per axis: central in the interior of an
+ *       axis, first-order one-sided on the first/last node of a walled axis,
+ *       central with wrap-around on a periodic axis.
+ *   R6  initial state: r0 = -rho0 tr(H0) (from d_t r + div j = 0), Pi0 = Pi(H0),
+ *       f0 = feq(r0, rho0 v0 - dt/2 S0, Pi0), so that the first moment j
+ *       evaluated by the algorithm equals rho0 v0.
+ *   R7  r^bd of the Neumann rule is the node's own r from block 1; every tensor
+ *       "extrapolated to the boundary" is the boundary node's own value; the
+ *       (P + Pi(H)) used there is the array as it stands when block 2 runs,
+ *       i.e. computed in block 3 of the previous iteration (or at initialisation).
+ *   R8  corners: each outgoing link takes the rule of the wall it crosses; a
+ *       diagonal link crossing two walls is Dirichlet if either wall is
+ *       (momentum: mean of the two walls' j* when both are); at a node on two
+ *       Neumann walls Pi*_xx comes from the x-wall, Pi*_yy from the y-wall and
+ *       Pi*_xy is the mean of the two walls' shear entries.
+ *   R9  a boundary value is evaluated at t_k = k dt of the iteration k that
+ *       applies it.
+ *
+ * Parity status: the building blocks are pinned by the CPU tests (moment
+ * identities, closed-form stresses, energy derivatives, FD exactness, rigid
+ * motions, stationary homogeneous states, wave speeds, conservation).  The
+ * paper's own error tables need its finite-element data, which is not
+ * available, so full trajectories are pinned only through those properties.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include "oracle.h"
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ---- D2Q9 velocity set (Tab. 1): c_q = c (EX[q], EY[q]), weights w_q ---- */
+static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                            1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+/* the direction opposite to q (q-bar) */
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+typedef double mat2[2][2];
+
+struct ora_sim {
+  ora_config cfg;
+  double mu, lam, cs, c, dt;
+  long k;       /* iteration counter, t_k = k dt */
+  long n;       /* number of nodes */
+  int per_x, per_y;
+  int order;
+  double *f;     /* [9][n] distributions at t_k (before collision)        */
+  double *fcoll; /* [9][n] post-collision distributions                   */
+  double *fnew;  /* [9][n] distributions at t_k + dt                      */
+  double *u;     /* [2][n] displacement                                   */
+  double *j;     /* [2][n] momentum density j(t_k) (block 4 / init)       */
+  double *jt;    /* [2][n] momentum density evaluated in block 1          */
+  double *S;     /* [2][n] source term as it stands                       */
+  double *P;     /* [4][n] P(H) as it stands                              */
+  double *Ph;    /* [4][n] Pi(H) as it stands                             */
+  double *r;     /* [n]    moment r from block 1                          */
+  double *Pi;    /* [3][n] moment Pi (xx, xy, yy) from block 1            */
+};
+
+/* ------------------------------------------------------------------------ */
+/* small 2x2 tensor helpers                                                  */
+
+static void mat_mul(const mat2 A, const mat2 B, mat2 C) {
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) C[a][b] = A[a][0] * B[0][b] + A[a][1] * B[1][b];
+}
+
+static void mat_transpose(const mat2 A, mat2 T) {
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) T[a][b] = A[b][a];
+}
+
+static double mat_det(const mat2 A) { return A[0][0] * A[1][1] - A[0][1] * A[1][0]; }
+
+static void mat_inverse(const mat2 A, mat2 Ai) {
+  double d = mat_det(A);
+  Ai[0][0] = A[1][1] / d;
+  Ai[0][1] = -A[0][1] / d;
+  Ai[1][0] = -A[1][0] / d;
+  Ai[1][1] = A[0][0] / d;
+}
+
+static double delta(int a, int b) { return a == b ? 1.0 : 0.0; }
+
+/* ------------------------------------------------------------------------ */
+/* parameters (Sect. 3.1/3.2, reading R4)                                   */
+
+void ora_params(const ora_config *cfg, double out[5]) {
+  double E = cfg->E, nu = cfg->nu;
+  double mu = E / (2.0 * (1.0 + nu));
+  double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  double cs = sqrt(mu / cfg->rho0); /* shear wave speed, Sect. 3.1 */
+  double c = sqrt(3.0) * cs;        /* lattice speed, Sect. 3.2      */
+  double dt = cfg->dx / c;          /* c = dX / dt, Sect. 2          */
+  out[0] = mu;
+  out[1] = lam;
+  out[2] = cs;
+  out[3] = c;
+  out[4] = dt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* constitutive laws (Sect. 4): E, C, J from H, S(E) or S(C, J), P = (H + 1) S */
+
+void ora_first_piola(int model, double lam, double mu, const double Hf[4], double Pf[4]) {
+  mat2 H = {{Hf[0], Hf[1]}, {Hf[2], Hf[3]}};
+  mat2 P;
+  if (model == ORA_LE) {
+    /* linear elastic comparison material: lam tr(H) I + mu (H + H^T) */
+    double trH = H[0][0] + H[1][1];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) P[a][b] = lam * trH * delta(a, b) + mu * (H[a][b] + H[b][a]);
+  } else {
+    mat2 F, Ft, C, Ht, HtH, E, S;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) F[a][b] = H[a][b] + delta(a, b);
+    mat_transpose(F, Ft);
+    mat_mul(Ft, F, C); /* C = (H + 1)^T (H + 1) */
+    mat_transpose(H, Ht);
+    mat_mul(Ht, H, HtH);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) E[a][b] = 0.5 * (Ht[a][b] + H[a][b] + HtH[a][b]);
+    double J = mat_det(F);
+    if (model == ORA_SVK) {
+      double trE = E[0][0] + E[1][1];
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) S[a][b] = lam * trE * delta(a, b) + 2.0 * mu * E[a][b];
+    } else { /* ORA_NH */
+      mat2 Ci;
+      mat_inverse(C, Ci);
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+          S[a][b] = 0.5 * lam * (J * J - 1.0) * Ci[a][b] + mu * (delta(a, b) - Ci[a][b]);
+    }
+    mat_mul(F, S, P); /* P = (H + 1) S */
+  }
+  Pf[0] = P[0][0];
+  Pf[1] = P[0][1];
+  Pf[2] = P[1][0];
+  Pf[3] = P[1][1];
+}
+
+/* constitutive momentum flux Pi(H) (reading R3) */
+void ora_pi_of_h(double mu, const double Hf[4], double Pif[4]) {
+  double trH = Hf[0] + Hf[3];
+  Pif[0] = -mu * (Hf[0] + Hf[0] + trH);
+  Pif[1] = -mu * (Hf[1] + Hf[2]);
+  Pif[2] = -mu * (Hf[2] + Hf[1]);
+  Pif[3] = -mu * (Hf[3] + Hf[3] + trH);
+}
+
+/* ------------------------------------------------------------------------ */
+/* equilibrium and forcing (Sect. 3.2)                                       */
+
+static void equilibrium_full(double cs, double c, double r, const double j[2], const mat2 Pi,
+                             double feq[9]) {
+  double cs2 = cs * cs;
+  for (int q = 0; q < 9; ++q) {
+    double cq[2] = {c * EX[q], c * EY[q]};
+    double cj = cq[0] * j[0] + cq[1] * j[1];
+    double contr = 0.0; /* (Pi - r cs^2 I) : (c_q c_q - cs^2 I) */
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        contr += (Pi[a][b] - r * cs2 * delta(a, b)) * (cq[a] * cq[b] - cs2 * delta(a, b));
+    feq[q] = W[q] * (r + cj / cs2 + contr / (2.0 * cs2 * cs2));
+  }
+}
+
+void ora_equilibrium(double cs, double r, const double j[2], const double Pif[4], double feq[9]) {
+  mat2 Pi = {{Pif[0], Pif[1]}, {Pif[2], Pif[3]}};
+  equilibrium_full(cs, sqrt(3.0) * cs, r, j, Pi, feq);
+}
+
+static void forcing_full(double cs, double c, const double S[2], double psi[9]) {
+  for (int q = 0; q < 9; ++q) psi[q] = W[q] * (c * EX[q] * S[0] + c * EY[q] * S[1]) / (cs * cs);
+}
+
+void ora_forcing(double cs, const double S[2], double psi[9]) {
+  forcing_full(cs, sqrt(3.0) * cs, S, psi);
+}
+
+/* ------------------------------------------------------------------------ */
+/* finite differences (Sect. 3.2, reading R5)                                */
+
+static long node(const ora_sim *s, int x, int y) { return (long)y * s->cfg.nx + x; }
+
+static double d_dx(const ora_sim *s, const double *a, int x, int y) {
+  int nx = s->cfg.nx;
+  double h = s->cfg.dx;
+  if (s->per_x) {
+    int xp = (x + 1) % nx, xm = (x - 1 + nx) % nx;
+    return (a[node(s, xp, y)] - a[node(s, xm, y)]) / (2.0 * h);
+  }
+  if (x == 0) return (a[node(s, 1, y)] - a[node(s, 0, y)]) / h;
+  if (x == nx - 1) return (a[node(s, nx - 1, y)] - a[node(s, nx - 2, y)]) / h;
+  return (a[node(s, x + 1, y)] - a[node(s, x - 1, y)]) / (2.0 * h);
+}
+
+static double d_dy(const ora_sim *s, const double *a, int x, int y) {
+  int ny = s->cfg.ny;
+  double h = s->cfg.dx;
+  if (s->per_y) {
+    int yp = (y + 1) % ny, ym = (y - 1 + ny) % ny;
+    return (a[node(s, x, yp)] - a[node(s, x, ym)]) / (2.0 * h);
+  }
+  if (y == 0) return (a[node(s, x, 1)] - a[node(s, x, 0)]) / h;
+  if (y == ny - 1) return (a[node(s, x, ny - 1)] - a[node(s, x, ny - 2)]) / h;
+  return (a[node(s, x, y + 1)] - a[node(s, x, y - 1)]) / (2.0 * h);
+}
+
+/* H_ab = d u_a / d X_b (Eq. defgrad) at every node; u is [2][n], H is [4][n] */
+static void gradient_all(const ora_sim *s, const double *u, double *H) {
+  long n = s->n;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < s->cfg.ny; ++y)
+    for (int x = 0; x < s->cfg.nx; ++x) {
+      long i = node(s, x, y);
+      H[0 * n + i] = d_dx(s, u + 0 * n, x, y);
+      H[1 * n + i] = d_dy(s, u + 0 * n, x, y);
+      H[2 * n + i] = d_dx(s, u + 1 * n, x, y);
+      H[3 * n + i] = d_dy(s, u + 1 * n, x, y);
+    }
+}
+
+/* block 3: H from u, then P(H) and Pi(H) at every node */
+static void stresses(ora_sim *s) {
+  long n = s->n;
+  double *H = malloc(sizeof(double) * 4 * n);
+  gradient_all(s, s->u, H);
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < n; ++i) {
+    double Hi[4] = {H[i], H[n + i], H[2 * n + i], H[3 * n + i]}, Pi_[4], Ph_[4];
+    ora_first_piola(s->cfg.model, s->lam, s->mu, Hi, Pi_);
+    ora_pi_of_h(s->mu, Hi, Ph_);
+    for (int m = 0; m < 4; ++m) {
+      s->P[m * n + i] = Pi_[m];
+      s->Ph[m * n + i] = Ph_[m];
+    }
+  }
+  free(H);
+}
+
+/* S = rho0 b + div(P + Pi(H)), (div N)_a = d N_ab / d X_b (Eq. source) */
+static void source(ora_sim *s) {
+  long n = s->n;
+  double *N = malloc(sizeof(double) * 4 * n);
+  for (long m = 0; m < 4 * n; ++m) N[m] = s->P[m] + s->Ph[m];
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < s->cfg.ny; ++y)
+    for (int x = 0; x < s->cfg.nx; ++x) {
+      long i = node(s, x, y);
+      s->S[0 * n + i] = s->cfg.rho0 * s->cfg.body[0] + d_dx(s, N + 0 * n, x, y) + d_dy(s, N + 1 * n, x, y);
+      s->S[1 * n + i] = s->cfg.rho0 * s->cfg.body[1] + d_dx(s, N + 2 * n, x, y) + d_dy(s, N + 3 * n, x, y);
+    }
+  free(N);
+}
+
+/* ------------------------------------------------------------------------ */
+/* prescribed boundary values (reading R9)                                   */
+
+void ora_load(const ora_config *cfg, int edge, long k, double out[2]) {
+  const ora_edge *e = &cfg->edge[edge];
+  double t = (double)k, f = 0.0;
+  double span = e->t1 - e->t0;
+  switch (e->shape) {
+    case ORA_CONST:
+      f = 1.0;
+      break;
+    case ORA_LINEAR_RAMP: {
+      double x = (t - e->t0) / span;
+      f = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+      break;
+    }
+    case ORA_SIN2_RAMP: {
+      double x = (t - e->t0) / span;
+      x = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+      double sn = sin(0.5 * M_PI * x);
+      f = sn * sn;
+      break;
+    }
+    case ORA_HALF_SINE:
+      f = (t >= e->t0 && t < e->t1) ? sin(M_PI * (t - e->t0) / span) : 0.0;
+      break;
+    case ORA_RICKER: {
+      double d = t - e->t0;
+      f = t < e->t1 ? (1.0 - d * d / e->s) * exp(-0.5 * d * d / e->s) : 0.0;
+      break;
+    }
+    case ORA_DISP_RAMP: {
+      double p[5];
+      ora_params(cfg, p);
+      f = (t >= e->t0 && t < e->t1) ? cfg->rho0 / (span * p[4]) : 0.0;
+      break;
+    }
+    default:
+      f = 0.0;
+  }
+  out[0] = e->amp[0] * f;
+  out[1] = e->amp[1] * f;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neumann momentum flux Pi* at a boundary node (Sect. 3.3, readings R7, R8) */
+
+/* quasi-boundary traction on a wall with outward unit normal N:
+ *   Pi* N = -T* + (P + Pi(H)) N  ->  first row and column of Pi* */
+static void wall_flux_column(const ora_sim *s, long i, int edge, double col[2]) {
+  long n = s->n;
+  double Nv[2] = {0.0, 0.0};
+  if (edge == ORA_LEFT) Nv[0] = -1.0;
+  if (edge == ORA_RIGHT) Nv[0] = 1.0;
+  if (edge == ORA_BOTTOM) Nv[1] = -1.0;
+  if (edge == ORA_TOP) Nv[1] = 1.0;
+  double T[2];
+  ora_load(&s->cfg, edge, s->k, T);
+  mat2 NP;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) NP[a][b] = s->P[(2 * a + b) * n + i] + s->Ph[(2 * a + b) * n + i];
+  int nd = (edge == ORA_LEFT || edge == ORA_RIGHT) ? 0 : 1;
+  for (int a = 0; a < 2; ++a) {
+    double q = -T[a] + NP[a][0] * Nv[0] + NP[a][1] * Nv[1];
+    col[a] = q / Nv[nd]; /* Pi*_{a n} N_n = q_a */
+  }
+}
+
+static void neumann_flux(const ora_sim *s, long i, int xwall, int ywall, mat2 Pis) {
+  long n = s->n;
+  /* start from the node's own moment (extrapolated entries) */
+  Pis[0][0] = s->Pi[0 * n + i];
+  Pis[0][1] = Pis[1][0] = s->Pi[1 * n + i];
+  Pis[1][1] = s->Pi[2 * n + i];
+  double cx[2], cy[2];
+  if (xwall >= 0) wall_flux_column(s, i, xwall, cx);
+  if (ywall >= 0) wall_flux_column(s, i, ywall, cy);
+  if (xwall >= 0 && ywall >= 0) {
+    Pis[0][0] = cx[0];
+    Pis[1][1] = cy[1];
+    Pis[0][1] = Pis[1][0] = 0.5 * (cx[1] + cy[0]);
+  } else if (xwall >= 0) {
+    Pis[0][0] = cx[0];
+    Pis[1][0] = Pis[0][1] = cx[1];
+  } else if (ywall >= 0) {
+    Pis[1][1] = cy[1];
+    Pis[0][1] = Pis[1][0] = cy[0];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* creation and initialisation (Alg. 1 "Initialise", reading R6)             */
+
+static int validate(const ora_config *c) {
+  if (c->nx < 3 || c->ny < 3) return 0;
+  if (!(c->tau > 0.5) || !(c->dx > 0.0) || !(c->rho0 > 0.0) || !(c->E > 0.0)) return 0;
+  if (!(c->nu > -1.0 && c->nu < 0.5)) return 0;
+  if (c->model < ORA_SVK || c->model > ORA_LE) return 0;
+  for (int e = 0; e < 4; ++e) {
+    const ora_edge *ed = &c->edge[e];
+    if (ed->type < ORA_PERIODIC || ed->type > ORA_NEUMANN) return 0;
+    if (ed->shape < ORA_CONST || ed->shape > ORA_DISP_RAMP) return 0;
+    if ((ed->shape == ORA_LINEAR_RAMP || ed->shape == ORA_SIN2_RAMP || ed->shape == ORA_HALF_SINE ||
+         ed->shape == ORA_DISP_RAMP) && !(ed->t1 > ed->t0))
+      return 0;
+    if (ed->shape == ORA_RICKER && !(ed->s > 0.0)) return 0;
+    if (ed->shape == ORA_DISP_RAMP && ed->type != ORA_DIRICHLET) return 0;
+  }
+  if (c->order != ORA_ORDER_TEXT && c->order != ORA_ORDER_LISTING) return 0;
+  if ((c->edge[ORA_LEFT].type == ORA_PERIODIC) != (c->edge[ORA_RIGHT].type == ORA_PERIODIC)) return 0;
+  if ((c->edge[ORA_BOTTOM].type == ORA_PERIODIC) != (c->edge[ORA_TOP].type == ORA_PERIODIC)) return 0;
+  return 1;
+}
+
+ora_sim *ora_create(const ora_config *cfg, const double *u0, const double *v0) {
+  if (!validate(cfg)) return NULL;
+  ora_sim *s = calloc(1, sizeof(ora_sim));
+  s->cfg = *cfg;
+  double p[5];
+  ora_params(cfg, p);
+  s->mu = p[0];
+  s->lam = p[1];
+  s->cs = p[2];
+  s->c = p[3];
+  s->dt = p[4];
+  s->n = (long)cfg->nx * cfg->ny;
+  s->per_x = cfg->edge[ORA_LEFT].type == ORA_PERIODIC;
+  s->per_y = cfg->edge[ORA_BOTTOM].type == ORA_PERIODIC;
+  s->order = cfg->order;
+  long n = s->n;
+  s->f = calloc(9 * n, sizeof(double));
+  s->fcoll = calloc(9 * n, sizeof(double));
+  s->fnew = calloc(9 * n, sizeof(double));
+  s->u = calloc(2 * n, sizeof(double));
+  s->j = calloc(2 * n, sizeof(double));
+  s->jt = calloc(2 * n, sizeof(double));
+  s->S = calloc(2 * n, sizeof(double));
+  s->P = calloc(4 * n, sizeof(double));
+  s->Ph = calloc(4 * n, sizeof(double));
+  s->r = calloc(n, sizeof(double));
+  s->Pi = calloc(3 * n, sizeof(double));
+
+  /* fields u, H, P, Pi(H) and the source S */
+  for (long i = 0; i < n; ++i) {
+    s->u[i] = u0 ? u0[2 * i] : 0.0;
+    s->u[n + i] = u0 ? u0[2 * i + 1] : 0.0;
+  }
+  stresses(s);
+  source(s);
+
+  /* moments r0 = -rho0 tr(H0), j0 = rho0 v0, Pi0 = Pi(H0); f <- feq */
+  double *H = malloc(sizeof(double) * 4 * n);
+  gradient_all(s, s->u, H);
+  for (long i = 0; i < n; ++i) {
+    double r0 = -cfg->rho0 * (H[i] + H[3 * n + i]);
+    double j0[2] = {cfg->rho0 * (v0 ? v0[2 * i] : 0.0), cfg->rho0 * (v0 ? v0[2 * i + 1] : 0.0)};
+    mat2 Pi0 = {{s->Ph[i], s->Ph[n + i]}, {s->Ph[2 * n + i], s->Ph[3 * n + i]}};
+    double jshift[2] = {j0[0] - 0.5 * s->dt * s->S[i], j0[1] - 0.5 * s->dt * s->S[n + i]};
+    double feq[9];
+    equilibrium_full(s->cs, s->c, r0, jshift, Pi0, feq);
+    for (int q = 0; q < 9; ++q) s->f[q * n + i] = feq[q];
+    s->j[i] = j0[0];
+    s->j[n + i] = j0[1];
+  }
+  free(H);
+  s->k = 0;
+  return s;
+}
+
+void ora_destroy(ora_sim *s) {
+  if (!s) return;
+  free(s->f);
+  free(s->fcoll);
+  free(s->fnew);
+  free(s->u);
+  free(s->j);
+  free(s->jt);
+  free(s->S);
+  free(s->P);
+  free(s->Ph);
+  free(s->r);
+  free(s->Pi);
+  free(s);
+}
+
+long ora_iteration(const ora_sim *s) { return s->k; }
+
+int ora_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* one iteration of Algorithm 1                                              */
+
+static void block1_collide_stream(ora_sim *s) {
+  long n = s->n;
+  int nx = s->cfg.nx, ny = s->cfg.ny;
+  double c = s->c, cs = s->cs, dt = s->dt, tau = s->cfg.tau;
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < n; ++i) {
+    double fq[9], feq[9], psi[9];
+    for (int q = 0; q < 9; ++q) fq[q] = s->f[q * n + i];
+    double S[2] = {s->S[i], s->S[n + i]};
+    /* moments: r, j (with dt/2 S), Pi */
+    double r = 0.0, jsum[2] = {0.0, 0.0};
+    mat2 Pi = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int q = 0; q < 9; ++q) {
+      double cq[2] = {c * EX[q], c * EY[q]};
+      r += fq[q];
+      for (int a = 0; a < 2; ++a) {
+        jsum[a] += cq[a] * fq[q];
+        for (int b = 0; b < 2; ++b) Pi[a][b] += cq[a] * cq[b] * fq[q];
+      }
+    }
+    double j[2] = {jsum[0] + 0.5 * dt * S[0], jsum[1] + 0.5 * dt * S[1]};
+    s->r[i] = r;
+    s->Pi[i] = Pi[0][0];
+    s->Pi[n + i] = Pi[0][1];
+    s->Pi[2 * n + i] = Pi[1][1];
+    s->jt[i] = j[0];
+    s->jt[n + i] = j[1];
+    equilibrium_full(cs, c, r, j, Pi, feq);
+    forcing_full(cs, c, S, psi);
+    for (int q = 0; q < 9; ++q)
+      s->fcoll[q * n + i] = fq[q] - (1.0 / tau) * (fq[q] - feq[q]) + (1.0 - 1.0 / (2.0 * tau)) * psi[q] * dt;
+  }
+  /* stream: f_q(X + c_q dt, t + dt) <- f_q^coll(X, t); unset entries stay NaN
+   * until the boundary block writes them */
+  for (long m = 0; m < 9 * n; ++m) s->fnew[m] = NAN;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x)
+      for (int q = 0; q < 9; ++q) {
+        int tx = x + EX[q], ty = y + EY[q];
+        if (s->per_x) tx = (tx + nx) % nx;
+        if (s->per_y) ty = (ty + ny) % ny;
+        if (tx < 0 || tx >= nx || ty < 0 || ty >= ny) continue;
+        s->fnew[q * n + node(s, tx, ty)] = s->fcoll[q * n + node(s, x, y)];
+      }
+}
+
+static void block2_boundaries(ora_sim *s) {
+  long n = s->n;
+  int nx = s->cfg.nx, ny = s->cfg.ny;
+  double c = s->c, cs = s->cs, cs2 = cs * cs;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      int on_x = !s->per_x && (x == 0 || x == nx - 1);
+      int on_y = !s->per_y && (y == 0 || y == ny - 1);
+      if (!on_x && !on_y) continue;
+      long i = node(s, x, y);
+      int xw = on_x ? (x == 0 ? ORA_LEFT : ORA_RIGHT) : -1;
+      int yw = on_y ? (y == 0 ? ORA_BOTTOM : ORA_TOP) : -1;
+      /* Neumann walls this node sits on (for Pi*) */
+      int xn = (xw >= 0 && s->cfg.edge[xw].type == ORA_NEUMANN) ? xw : -1;
+      int yn = (yw >= 0 && s->cfg.edge[yw].type == ORA_NEUMANN) ? yw : -1;
+      for (int q = 1; q < 9; ++q) {
+        int tx = x + EX[q], ty = y + EY[q];
+        int ox = !s->per_x && (tx < 0 || tx >= nx);
+        int oy = !s->per_y && (ty < 0 || ty >= ny);
+        if (!ox && !oy) continue; /* link q stays inside the lattice */
+        int wx = ox ? (tx < 0 ? ORA_LEFT : ORA_RIGHT) : -1;
+        int wy = oy ? (ty < 0 ? ORA_BOTTOM : ORA_TOP) : -1;
+        int dir_x = wx >= 0 && s->cfg.edge[wx].type == ORA_DIRICHLET;
+        int dir_y = wy >= 0 && s->cfg.edge[wy].type == ORA_DIRICHLET;
+        double cq[2] = {c * EX[q], c * EY[q]};
+        double fc = s->fcoll[q * n + i];
+        double out;
+        if (dir_x || dir_y) {
+          /* Eq. (bbcon): f_qbar = f_q^coll - 2/cs^2 w_q c_q . j* */
+          double js[2] = {0.0, 0.0};
+          if (dir_x && dir_y) {
+            double a[2], b[2];
+            ora_load(&s->cfg, wx, s->k, a);
+            ora_load(&s->cfg, wy, s->k, b);
+            js[0] = 0.5 * (a[0] + b[0]);
+            js[1] = 0.5 * (a[1] + b[1]);
+          } else {
+            ora_load(&s->cfg, dir_x ? wx : wy, s->k, js);
+          }
+          out = fc - 2.0 / cs2 * W[q] * (cq[0] * js[0] + cq[1] * js[1]);
+        } else {
+          /* Eq. (abbcon): f_qbar = -f_q^coll + 2 w_q (r + (Pi* - r cs^2 I):(c c - cs^2 I)/(2 cs^4)) */
+          mat2 Pis;
+          int use_x = (xn >= 0 && yn >= 0) ? xn : (wx >= 0 ? wx : -1);
+          int use_y = (xn >= 0 && yn >= 0) ? yn : (wy >= 0 ? wy : -1);
+          neumann_flux(s, i, use_x, use_y, Pis);
+          double rbd = s->r[i];
+          double contr = 0.0;
+          for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+              contr += (Pis[a][b] - rbd * cs2 * delta(a, b)) * (cq[a] * cq[b] - cs2 * delta(a, b));
+          out = -fc + 2.0 * W[q] * (rbd + contr / (2.0 * cs2 * cs2));
+        }
+        s->fnew[OPP[q] * n + i] = out;
+      }
+    }
+}
+
+/* j(t + dt) and the trapezoidal displacement update; S is the array as it
+ * stands (evaluated at t, Sect. 3.1 note on the source time level) */
+static void update_displacement(ora_sim *s) {
+  long n = s->n;
+  double c = s->c, dt = s->dt, rho0 = s->cfg.rho0;
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < n; ++i) {
+    double jsum[2] = {0.0, 0.0};
+    for (int q = 0; q < 9; ++q) {
+      jsum[0] += c * EX[q] * s->fnew[q * n + i];
+      jsum[1] += c * EY[q] * s->fnew[q * n + i];
+    }
+    for (int a = 0; a < 2; ++a) {
+      double jn = jsum[a] + 0.5 * dt * s->S[a * n + i];
+      s->u[a * n + i] = s->u[a * n + i] + dt / (2.0 * rho0) * (jn + s->jt[a * n + i]);
+      s->j[a * n + i] = jn;
+    }
+  }
+}
+
+void ora_step(ora_sim *s, long nsteps) {
+  for (long it = 0; it < nsteps; ++it) {
+    block1_collide_stream(s);
+    block2_boundaries(s);
+    if (s->order == ORA_ORDER_LISTING) {
+      stresses(s); /* H from u(t_k) */
+      source(s);
+      update_displacement(s);
+    } else {
+      update_displacement(s);
+      stresses(s); /* H from u(t_k + dt): the next collision uses S(t_k + dt) */
+      source(s);
+    }
+    double *tmp = s->f;
+    s->f = s->fnew;
+    s->fnew = tmp;
+    s->k += 1;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* outputs                                                                   */
+
+void ora_gradient(const ora_config *cfg, const double *u_aos, double *H_aos) {
+  ora_sim tmp;
+  memset(&tmp, 0, sizeof(tmp));
+  tmp.cfg = *cfg;
+  tmp.n = (long)cfg->nx * cfg->ny;
+  tmp.per_x = cfg->edge[ORA_LEFT].type == ORA_PERIODIC;
+  tmp.per_y = cfg->edge[ORA_BOTTOM].type == ORA_PERIODIC;
+  long n = tmp.n;
+  double *u = malloc(sizeof(double) * 2 * n), *H = malloc(sizeof(double) * 4 * n);
+  for (long i = 0; i < n; ++i) {
+    u[i] = u_aos[2 * i];
+    u[n + i] = u_aos[2 * i + 1];
+  }
+  gradient_all(&tmp, u, H);
+  for (long i = 0; i < n; ++i)
+    for (int m = 0; m < 4; ++m) H_aos[4 * i + m] = H[m * n + i];
+  free(u);
+  free(H);
+}
+
+void ora_fields(const ora_sim *s, double *u, double *v, double *P) {
+  long n = s->n;
+  if (u)
+    for (long i = 0; i < n; ++i) {
+      u[2 * i] = s->u[i];
+      u[2 * i + 1] = s->u[n + i];
+    }
+  if (v)
+    for (long i = 0; i < n; ++i) {
+      v[2 * i] = s->j[i] / s->cfg.rho0;
+      v[2 * i + 1] = s->j[n + i] / s->cfg.rho0;
+    }
+  if (P) {
+    double *H = malloc(sizeof(double) * 4 * n);
+    gradient_all(s, s->u, H);
+    for (long i = 0; i < n; ++i) {
+      double Hi[4] = {H[i], H[n + i], H[2 * n + i], H[3 * n + i]};
+      ora_first_piola(s->cfg.model, s->lam, s->mu, Hi, P + 4 * i);
+    }
+    free(H);
+  }
+}
