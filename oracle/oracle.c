@@ -659,9 +659,16 @@ void ora_fields(const ora_sim *s, double *u, double *v, double *P) {
       u[2 * i + 1] = s->u[n + i];
     }
   if (v)
+    /* the momentum the collision at the current time uses (Alg. 1, first
+     * block): j = sum_q c_q f_q + dt/2 S with S = S(u(t)) */
     for (long i = 0; i < n; ++i) {
-      v[2 * i] = s->j[i] / s->cfg.rho0;
-      v[2 * i + 1] = s->j[n + i] / s->cfg.rho0;
+      double jx = 0.0, jy = 0.0;
+      for (int q = 0; q < 9; ++q) {
+        jx += s->c * EX[q] * s->f[q * n + i];
+        jy += s->c * EY[q] * s->f[q * n + i];
+      }
+      v[2 * i] = (jx + 0.5 * s->dt * s->S[i]) / s->cfg.rho0;
+      v[2 * i + 1] = (jy + 0.5 * s->dt * s->S[n + i]) / s->cfg.rho0;
     }
   if (P) {
     double *H = malloc(sizeof(double) * 4 * n);

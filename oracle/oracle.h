@@ -73,7 +73,8 @@ void ora_params(const ora_config *cfg, double out[5]); /* mu, lam, cs, c, dt */
 ora_sim *ora_create(const ora_config *cfg, const double *u0, const double *v0);
 void ora_step(ora_sim *s, long n);
 long ora_iteration(const ora_sim *s);
-/* u, v (= j / rho0) and P(H(u)) at the current time; any pointer may be NULL. */
+/* u, v = j / rho0 with j = sum_q c_q f_q + dt/2 S (the momentum that the
+ * collision at the current time uses) and P(H(u)); any pointer may be NULL. */
 void ora_fields(const ora_sim *s, double *u, double *v, double *P);
 void ora_destroy(ora_sim *s);
 int ora_threads(void);

@@ -1,0 +1,46 @@
+// FP64 storage and arithmetic: kernel instantiations and launchers of liblbs.
+#include "lbs_device.cuh"
+
+namespace lbs {
+namespace {
+using P = F64;
+// tile variants (nodes along x, nodes along y, thread rows)
+using V0 = Cfg<P, 32, 16, 8>;
+using V1 = Cfg<P, 32, 8, 8>;
+using V2 = Cfg<P, 64, 8, 4>;
+using V3 = Cfg<P, 32, 32, 8>;
+constexpr int kVariants = 4;
+
+TileShape shape(int v) {
+  switch (v) {
+    case 1: return {V1::TX, V1::TY};
+    case 2: return {V2::TX, V2::TY};
+    case 3: return {V3::TX, V3::TY};
+    default: return {V0::TX, V0::TY};
+  }
+}
+
+cudaError_t step(const Params &p, const StepPtrs &s, int v, cudaStream_t st) {
+  switch (v) {
+    case 1: return launch_step<V1>(p, s, st);
+    case 2: return launch_step<V2>(p, s, st);
+    case 3: return launch_step<V3>(p, s, st);
+    default: return launch_step<V0>(p, s, st);
+  }
+}
+
+const Launchers kL = {kVariants,
+                      shape,
+                      step,
+                      launch_init<V0>,
+                      launch_fields<V0>,
+                      launch_monitor<V0>,
+                      launch_probe<V0>,
+                      sizeof(typename P::gs),
+                      sizeof(typename P::us),
+                      sizeof(typename P::real)};
+}  // namespace
+
+const Launchers &launchers_fp64() { return kL; }
+
+}  // namespace lbs

@@ -1,0 +1,876 @@
+// Device code of liblbs: the fused per-iteration update of the moment-chain
+// lattice Boltzmann method for non-linear solids (arXiv 2502.00920,
+// Algorithm 1), plus the initialisation, field-output, monitor and probe
+// kernels.  Included by kernels_fp64.cu / kernels_fp32.cu / kernels_fp16.cu,
+// each of which instantiates it for one storage precision.
+//
+// State between iterations (per node): the post-collision distributions g
+// (9 values) and the displacement u.  One fused kernel per iteration k:
+//   1. on the tile plus a 2-node halo: pull-stream g_k (bounce-back /
+//      anti-bounce-back where the source lies outside, Eq. bbcon / abbcon)
+//      and advance u with the trapezoidal rule,
+//        u_{k+1} = u_k + dt/(2 rho0) (sum_q c_q g_k,q + sum_q c_q f_{k+1,q}),
+//      which equals dt/(2 rho0) (j(t+dt) + j(t)) of Sect. 3.2 because the
+//      collision adds dt S to the first moment;
+//   2. on the tile plus a 1-node halo: H = grad u_{k+1} by finite
+//      differences and N = P(H) + Pi(H) (Eq. source);
+//   3. on the tile: S = rho0 b + div N, BGK collision of f_{k+1} with the
+//      forcing term (Alg. 1), store g_{k+1} and u_{k+1}; on wall nodes store
+//      N for the Neumann rule of the next iteration.
+// The collision at t therefore uses S(u(t)), as Sect. 3.1 requires.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lbs_internal.h"
+
+namespace lbs {
+
+// ------------------------------------------------------------------ D2Q9
+// Tab. 1: c_q = c (ex(q), ey(q)); weights 4/9, 1/9 (axes), 1/36 (diagonals)
+__host__ __device__ constexpr int ex(int q) { return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0); }
+__host__ __device__ constexpr int ey(int q) { return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0); }
+__host__ __device__ constexpr int opp(int q) { return q == 0 ? 0 : (q <= 4 ? ((q + 1) % 4) + 1 : ((q - 3) % 4) + 5); }
+template <class R>
+__host__ __device__ constexpr R wq(int q) { return q == 0 ? R(4) / R(9) : (q <= 4 ? R(1) / R(9) : R(1) / R(36)); }
+
+// ------------------------------------------------------------------ precision
+struct F64 {
+  using real = double;
+  using gs = double;
+  using us = double2;
+  static constexpr int id = LBS_FP64;
+};
+struct F32 {
+  using real = float;
+  using gs = float;
+  using us = float4;  // (hi_x, hi_y, lo_x, lo_y): u = hi + lo
+  static constexpr int id = LBS_FP32;
+};
+struct F16 {
+  using real = float;
+  using gs = __half;  // g * 2^gshift
+  using us = float4;
+  static constexpr int id = LBS_FP16S;
+};
+
+__device__ __forceinline__ double gload(const double *p, size_t i, double) { return __ldg(p + i); }
+__device__ __forceinline__ float gload(const float *p, size_t i, float) { return __ldg(p + i); }
+__device__ __forceinline__ float gload(const __half *p, size_t i, float inv) { return __half2float(__ldg(p + i)) * inv; }
+__device__ __forceinline__ void gstore(double *p, size_t i, double v, double) { p[i] = v; }
+__device__ __forceinline__ void gstore(float *p, size_t i, float v, float) { p[i] = v; }
+__device__ __forceinline__ void gstore(__half *p, size_t i, float v, float s) { p[i] = __float2half_rn(v * s); }
+
+// difference of two displacement records, as the compute type
+__device__ __forceinline__ void udiff(const double2 &a, const double2 &b, double &dx, double &dy) {
+  dx = a.x - b.x;
+  dy = a.y - b.y;
+}
+// hi parts of neighbouring nodes are close, so their difference is exact or
+// correctly rounded; the lo parts carry what lies below the hi ulp
+__device__ __forceinline__ void udiff(const float4 &a, const float4 &b, float &dx, float &dy) {
+  dx = (a.x - b.x) + (a.z - b.z);
+  dy = (a.y - b.y) + (a.w - b.w);
+}
+
+__device__ __forceinline__ double2 uadd(const double2 &u, double dx, double dy) { return make_double2(u.x + dx, u.y + dy); }
+
+// compensated accumulation: (hi, lo) + d with the rounding error of hi + d
+// (two-sum, Knuth) folded into lo, then renormalised (fast two-sum)
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float d) {
+  float s = hi + d;
+  float bp = s - hi;
+  float e = (hi - (s - bp)) + (d - bp);
+  float l = lo + e;
+  float h2 = s + l;
+  lo = l - (h2 - s);
+  hi = h2;
+}
+__device__ __forceinline__ float4 uadd(const float4 &u, float dx, float dy) {
+  float4 r = u;
+  pair_add(r.x, r.z, dx);
+  pair_add(r.y, r.w, dy);
+  return r;
+}
+
+__device__ __forceinline__ double2 u_value(const double2 &u) { return u; }
+__device__ __forceinline__ double2 u_value(const float4 &u) {
+  return make_double2((double)u.x + (double)u.z, (double)u.y + (double)u.w);
+}
+__device__ __forceinline__ void u_make(double x, double y, double2 &out) { out = make_double2(x, y); }
+__device__ __forceinline__ void u_make(double x, double y, float4 &out) {
+  float hx = (float)x, hy = (float)y;
+  out = make_float4(hx, hy, (float)(x - (double)hx), (float)(y - (double)hy));
+}
+
+// ------------------------------------------------------------------ material
+// N(H) = P(H) + Pi(H), Pi(H) = -mu (H + H^T + tr H I), written so that no
+// term cancels at small strain (Sect. 4 laws, rearranged):
+//   SVK: N = (lam trE - mu trH) I + mu H^T H + H S,  S = lam trE I + mu (H + H^T + H^T H)
+//   NH : with a = J - 1 = trH + detH, K = trH I - H^T (cof F = I + K),
+//        N = (mu/J) (-a H^T + (a - (2 + a) trH) I) + lam a (a + 2) / (2 J) (I + K)
+//   LE : N = (lam - mu) trH I
+// H = (H11, H12, H21, H22), H_ab = d u_a / d X_b.
+template <class R>
+__host__ __device__ inline void constitutive_n(int model, R lam, R mu, const R H[4], R N[4]) {
+  const R h11 = H[0], h12 = H[1], h21 = H[2], h22 = H[3];
+  const R trH = h11 + h22;
+  if (model == LBS_LE) {
+    const R d = (lam - mu) * trH;
+    N[0] = d;
+    N[1] = R(0);
+    N[2] = R(0);
+    N[3] = d;
+  } else if (model == LBS_SVK) {
+    // H^T H
+    const R c11 = h11 * h11 + h21 * h21, c12 = h11 * h12 + h21 * h22, c22 = h12 * h12 + h22 * h22;
+    const R trE = trH + R(0.5) * (c11 + c22);
+    const R s11 = lam * trE + mu * (R(2) * h11 + c11);
+    const R s12 = mu * (h12 + h21 + c12);
+    const R s22 = lam * trE + mu * (R(2) * h22 + c22);
+    const R d = lam * trE - mu * trH;
+    N[0] = d + mu * c11 + h11 * s11 + h12 * s12;
+    N[1] = mu * c12 + h11 * s12 + h12 * s22;
+    N[2] = mu * c12 + h21 * s11 + h22 * s12;
+    N[3] = d + mu * c22 + h21 * s12 + h22 * s22;
+  } else {  // LBS_NH
+    const R detH = h11 * h22 - h12 * h21;
+    const R a = trH + detH;
+    const R J = R(1) + a;
+    const R iJ = R(1) / J;
+    const R m = mu * iJ;
+    const R l = R(0.5) * lam * a * (a + R(2)) * iJ;
+    const R diag = m * (a - (R(2) + a) * trH);
+    // I + K = [[1 + h22, -h21], [-h12, 1 + h11]]
+    N[0] = -m * a * h11 + diag + l * (R(1) + h22);
+    N[1] = -m * a * h21 - l * h21;
+    N[2] = -m * a * h12 - l * h12;
+    N[3] = -m * a * h22 + diag + l * (R(1) + h11);
+  }
+}
+
+// N in the compute type; the FP32 kernels evaluate neo-Hooke in double where
+// J is small (near det F -> 0 the 1/J terms lose float accuracy)
+template <class R>
+__device__ __forceinline__ void material(const Params &P, R lam, R mu, const R H[4], R N[4]) {
+  if (sizeof(R) == 4 && P.model == LBS_NH) {
+    const R J = R(1) + (H[0] + H[3]) + (H[0] * H[3] - H[1] * H[2]);
+    if (J < R(0.5)) {
+      double Hd[4] = {H[0], H[1], H[2], H[3]}, Nd[4];
+      constitutive_n<double>(P.model, P.lam, P.mu, Hd, Nd);
+      for (int m = 0; m < 4; ++m) N[m] = (R)Nd[m];
+      return;
+    }
+  }
+  constitutive_n<R>(P.model, lam, mu, H, N);
+}
+
+// ------------------------------------------------------------------ loads
+// prescribed boundary value amp * s(k) of edge e at iteration k
+__device__ inline void edge_value(const Params &P, int e, int64_t k, double out[2]) {
+  const double t = (double)k, t0 = P.et0[e], t1 = P.et1[e], span = t1 - t0;
+  double f;
+  switch (P.eshape[e]) {
+    case LBS_CONST: f = 1.0; break;
+    case LBS_LINEAR_RAMP: f = fmin(fmax((t - t0) / span, 0.0), 1.0); break;
+    case LBS_SIN2_RAMP: {
+      const double sn = sin(0.5 * M_PI * fmin(fmax((t - t0) / span, 0.0), 1.0));
+      f = sn * sn;
+      break;
+    }
+    case LBS_HALF_SINE: f = (t >= t0 && t < t1) ? sin(M_PI * (t - t0) / span) : 0.0; break;
+    case LBS_RICKER: {
+      const double d = t - t0;
+      f = t < t1 ? (1.0 - d * d / P.es[e]) * exp(-0.5 * d * d / P.es[e]) : 0.0;
+      break;
+    }
+    case LBS_DISP_RAMP: f = (t >= t0 && t < t1) ? P.rho0 / (span * P.dt) : 0.0; break;
+    default: f = 0.0;
+  }
+  out[0] = P.eamp[e][0] * f;
+  out[1] = P.eamp[e][1] * f;
+}
+
+// ------------------------------------------------------------------ boundary rules
+// Pull-form boundary rules at a wall node (x, y): for every direction q whose
+// source x - c_q dt lies outside the lattice (bit q of `mask`), the outgoing
+// link qbar = opp(q) crosses a wall and f_q(x) is set from the node's own
+// post-collision g (Sect. 3.3):
+//   Dirichlet (Eq. bbcon):   f_q = g_qbar + 2 w_q c_q . j* / cs^2
+//   Neumann   (Eq. abbcon):  f_q = -g_qbar + 2 w_q (r + (Pi* - r cs^2 I):(c_q c_q - cs^2 I) / (2 cs^4))
+// with r and the tangential Pi entry from the node's own moments, and the
+// normal row/column of Pi* from -T* + (P + Pi(H)) N (N of this node, stored by
+// the previous iteration).  A diagonal link crossing two walls is Dirichlet if
+// either wall is (mean j* if both); at a node on two Neumann walls Pi*_xx
+// comes from the x wall, Pi*_yy from the y wall and Pi*_xy is the mean.
+template <class R>
+__device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t k, const R g0[9], unsigned mask,
+                           R f[9]) {
+  int xw = -1, yw = -1;
+  if (!P.per_x) xw = (x == 0) ? kLeft : ((x == P.nx - 1) ? kRight : -1);
+  if (!P.per_y) yw = (y == 0) ? kBottom : ((y == P.ny - 1) ? kTop : -1);
+  const bool xn = xw >= 0 && P.etype[xw] == LBS_NEUMANN;
+  const bool yn = yw >= 0 && P.etype[yw] == LBS_NEUMANN;
+  const R ics2 = (R)P.inv_cs2;
+  // own moments (collision leaves r and Pi unchanged): r, A = Pi / cs^2 = 3 sum e e g
+  R r = 0, mxx = 0, mxy = 0, myy = 0;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    r += g0[q];
+    mxx += R(ex(q) * ex(q)) * g0[q];
+    mxy += R(ex(q) * ey(q)) * g0[q];
+    myy += R(ey(q) * ey(q)) * g0[q];
+  }
+  R Axx = R(3) * mxx, Axy = R(3) * mxy, Ayy = R(3) * myy;
+  if (xn || yn) {
+    R axy_x = 0, axy_y = 0;
+    if (xn) {
+      const R *Nn = bnd + ((size_t)xw * P.blen + y) * 4;  // N11, N12, N21, N22
+      double T[2];
+      edge_value(P, xw, k, T);
+      const R s = (xw == kRight) ? R(1) : R(-1);
+      Axx = (Nn[0] - s * (R)T[0]) * ics2;
+      axy_x = (Nn[2] - s * (R)T[1]) * ics2;
+    }
+    if (yn) {
+      const R *Nn = bnd + ((size_t)yw * P.blen + x) * 4;
+      double T[2];
+      edge_value(P, yw, k, T);
+      const R s = (yw == kTop) ? R(1) : R(-1);
+      Ayy = (Nn[3] - s * (R)T[1]) * ics2;
+      axy_y = (Nn[1] - s * (R)T[0]) * ics2;
+    }
+    Axy = (xn && yn) ? R(0.5) * (axy_x + axy_y) : (xn ? axy_x : axy_y);
+  }
+  const R trA = Axx + Ayy;
+  const R cj = (R)(P.c * P.inv_cs2);
+#pragma unroll
+  for (int q = 1; q < 9; ++q) {
+    if (!(mask & (1u << q))) continue;
+    const bool ox = !P.per_x && ((ex(q) == 1 && x == 0) || (ex(q) == -1 && x == P.nx - 1));
+    const bool oy = !P.per_y && ((ey(q) == 1 && y == 0) || (ey(q) == -1 && y == P.ny - 1));
+    const bool dxw = ox && P.etype[xw] == LBS_DIRICHLET;
+    const bool dyw = oy && P.etype[yw] == LBS_DIRICHLET;
+    const int qb = opp(q);
+    if (dxw || dyw) {
+      double js[2];
+      if (dxw && dyw) {
+        double a[2], b[2];
+        edge_value(P, xw, k, a);
+        edge_value(P, yw, k, b);
+        js[0] = 0.5 * (a[0] + b[0]);
+        js[1] = 0.5 * (a[1] + b[1]);
+      } else {
+        edge_value(P, dxw ? xw : yw, k, js);
+      }
+      f[q] = g0[qb] + R(2) * wq<R>(q) * cj * (R(ex(q)) * (R)js[0] + R(ey(q)) * (R)js[1]);
+    } else {
+      const R e2 = R(ex(q) * ex(q) + ey(q) * ey(q));
+      const R eAe = R(ex(q) * ex(q)) * Axx + R(2 * ex(q) * ey(q)) * Axy + R(ey(q) * ey(q)) * Ayy;
+      f[q] = -g0[qb] + wq<R>(q) * (R(4) * r - R(3) * r * e2 + R(3) * eAe - trA);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ collision
+// BGK collision with forcing (Alg. 1): g = f - (f - feq)/tau + (1 - 1/(2 tau)) psi dt
+// in reduced variables: jj = c j / cs^2 = 3 sum e f + (sigma/2) S,
+// A = Pi / cs^2 = 3 sum e e f, sigma = c dt / cs^2,
+// feq_q = w_q (r (2 - 3|e|^2/2) + e.jj + 3/2 e.A.e - trA/2),
+// (1 - 1/(2 tau)) psi_q dt = w_q e.F, F = (1 - omega/2) sigma S.
+template <class R>
+__device__ __forceinline__ void collide(R f[9], R Sx, R Sy, R omega, R sigma) {
+  R r = 0, m1x = 0, m1y = 0, mxx = 0, mxy = 0, myy = 0;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    r += f[q];
+    if (ex(q)) m1x += R(ex(q)) * f[q];
+    if (ey(q)) m1y += R(ey(q)) * f[q];
+    if (ex(q)) mxx += f[q];
+    if (ex(q) * ey(q)) mxy += R(ex(q) * ey(q)) * f[q];
+    if (ey(q)) myy += f[q];
+  }
+  const R jx = R(3) * m1x + R(0.5) * sigma * Sx;
+  const R jy = R(3) * m1y + R(0.5) * sigma * Sy;
+  const R Axx = R(3) * mxx, Axy = R(3) * mxy, Ayy = R(3) * myy;
+  const R half_trA = R(0.5) * (Axx + Ayy);
+  const R fs = (R(1) - R(0.5) * omega) * sigma;
+  const R Fx = fs * Sx, Fy = fs * Sy;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const int e2 = ex(q) * ex(q) + ey(q) * ey(q);
+    const R rq = (e2 == 0) ? R(2) * r : ((e2 == 1) ? R(0.5) * r : -r);
+    const R eAe = R(ex(q) * ex(q)) * Axx + R(2 * ex(q) * ey(q)) * Axy + R(ey(q) * ey(q)) * Ayy;
+    const R ej = R(ex(q)) * jx + R(ey(q)) * jy;
+    const R eF = R(ex(q)) * Fx + R(ey(q)) * Fy;
+    const R feq = wq<R>(q) * (rq + ej + R(1.5) * eAe - half_trA);
+    f[q] = f[q] - omega * (f[q] - feq) + wq<R>(q) * eF;
+  }
+}
+
+// ------------------------------------------------------------------ tiles
+// A thread block owns a TX x TY tile of nodes; NTY thread rows, each thread
+// handles CPT = TY / NTY nodes of one column.  Shared memory holds u_{k+1}
+// on the tile plus a 2-node halo (R2) and N on the tile plus a 1-node halo (R1).
+template <class Pr, int TX_, int TY_, int NTY_>
+struct TileCfg {
+  using real = typename Pr::real;
+  using us = typename Pr::us;
+  using gs = typename Pr::gs;
+  static constexpr int TX = TX_, TY = TY_, NTY = NTY_;
+  static constexpr int NT = TX * NTY, CPT = TY / NTY;
+  static constexpr int R2W = TX + 4, R2H = TY + 4, R1W = TX + 2, R1H = TY + 2;
+  static constexpr int NRING = R2W * R2H - TX * TY;
+  struct Smem {
+    us u[R2H][R2W];
+    real n[4][R1H][R1W];
+  };
+  static_assert(TY % NTY == 0, "tile rows must split evenly over thread rows");
+};
+
+// position of ring entry r of R2 (the 2-node frame around the tile)
+template <class C>
+__device__ __forceinline__ void ring_pos(int r, int &rx, int &ry) {
+  constexpr int top = 2 * C::R2W;
+  if (r < top) {
+    ry = r / C::R2W;
+    rx = r % C::R2W;
+  } else if (r < 2 * top) {
+    r -= top;
+    ry = C::TY + 2 + r / C::R2W;
+    rx = r % C::R2W;
+  } else {
+    r -= 2 * top;
+    ry = 2 + r / 4;
+    const int c = r % 4;
+    rx = c < 2 ? c : C::TX + c;
+  }
+}
+
+// wrap (periodic) or reject a node coordinate; returns false outside
+__device__ __forceinline__ bool locate(const Params &P, int &x, int &y) {
+  if (x < 0 || x >= P.nx) {
+    if (!P.per_x) return false;
+    x = (x + P.nx) % P.nx;
+  }
+  if (y < 0 || y >= P.ny) {
+    if (!P.per_y) return false;
+    y = (y + P.ny) % P.ny;
+  }
+  return true;
+}
+
+// Stream into node (x, y) (already wrapped into the lattice) and return the
+// first moments sum_q e_q g_q (own node, post-collision at k) and
+// sum_q e_q f_q (streamed, at k + 1).  EDGE: wrap, walls and boundary rules.
+template <class Pr, bool EDGE>
+__device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *__restrict__ g, const typename Pr::real *bnd,
+                                       int x, int y, int64_t k, typename Pr::real inv, typename Pr::real f[9],
+                                       typename Pr::real &gx, typename Pr::real &gy) {
+  using R = typename Pr::real;
+  const size_t plane = (size_t)P.ny * P.pitch;
+  const size_t idx = (size_t)y * P.pitch + x;
+  R g0[9];
+  if (!EDGE) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = gload(g, q * plane + idx - ex(q) - (ptrdiff_t)ey(q) * P.pitch, inv);
+#pragma unroll
+    for (int q = 1; q < 9; ++q) g0[q] = gload(g, q * plane + idx, inv);
+    g0[0] = 0;
+  } else {
+    unsigned mask = 0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      g0[q] = gload(g, q * plane + idx, inv);
+      int sx = x - ex(q), sy = y - ey(q);
+      bool out = false;
+      if (sx < 0 || sx >= P.nx) {
+        if (P.per_x) sx = (sx + P.nx) % P.nx;
+        else out = true;
+      }
+      if (sy < 0 || sy >= P.ny) {
+        if (P.per_y) sy = (sy + P.ny) % P.ny;
+        else out = true;
+      }
+      if (out) {
+        mask |= 1u << q;
+        f[q] = 0;
+      } else {
+        f[q] = gload(g, q * plane + (size_t)sy * P.pitch + sx, inv);
+      }
+    }
+    if (mask) wall_rules<R>(P, bnd, x, y, k, g0, mask, f);
+  }
+  gx = (g0[1] - g0[3]) + (g0[5] - g0[6]) + (g0[8] - g0[7]);
+  gy = (g0[2] - g0[4]) + (g0[5] - g0[8]) + (g0[6] - g0[7]);
+}
+
+__device__ __forceinline__ bool on_wall(const Params &P, int x, int y) {
+  return (!P.per_x && (x == 0 || x == P.nx - 1)) || (!P.per_y && (y == 0 || y == P.ny - 1));
+}
+
+// store N of wall node (x, y) into the side array entries of its walls
+template <class R>
+__device__ __forceinline__ void store_wall_n(const Params &P, R *bnd, int x, int y, const R N[4]) {
+  if (!P.per_x && (x == 0 || x == P.nx - 1)) {
+    R *d = bnd + ((size_t)(x == 0 ? kLeft : kRight) * P.blen + y) * 4;
+    for (int m = 0; m < 4; ++m) d[m] = N[m];
+  }
+  if (!P.per_y && (y == 0 || y == P.ny - 1)) {
+    R *d = bnd + ((size_t)(y == 0 ? kBottom : kTop) * P.blen + x) * 4;
+    for (int m = 0; m < 4; ++m) d[m] = N[m];
+  }
+}
+
+// d/dX of a shared-memory row: central inside, one-sided on the first and
+// last node of a walled axis (Sect. 3.2); `lo`/`hi` say the node is such a
+// wall node.  Returns the difference already divided by the spacing.
+template <class C, bool EDGE>
+struct Fd {
+  using R = typename C::real;
+  // H at R1 position (rx, ry) from su (R2 coords = R1 + 1)
+  static __device__ __forceinline__ void grad(const typename C::Smem &sm, const Params &P, int rx, int ry, int gxn,
+                                              int gyn, R idx_, R H[4]) {
+    R dxx, dxy, dyx, dyy;  // d u_x/dx, d u_y/dx, d u_x/dy, d u_y/dy
+    const int cx = rx + 1, cy = ry + 1;
+    R sx = R(0.5) * idx_, sy = R(0.5) * idx_;
+    int xa = cx + 1, xb = cx - 1, ya = cy + 1, yb = cy - 1;
+    if (EDGE) {
+      if (!P.per_x) {
+        if (gxn == 0) { xb = cx; sx = idx_; }
+        else if (gxn == P.nx - 1) { xa = cx; sx = idx_; }
+      }
+      if (!P.per_y) {
+        if (gyn == 0) { yb = cy; sy = idx_; }
+        else if (gyn == P.ny - 1) { ya = cy; sy = idx_; }
+      }
+    }
+    udiff(sm.u[cy][xa], sm.u[cy][xb], dxx, dxy);
+    udiff(sm.u[ya][cx], sm.u[yb][cx], dyx, dyy);
+    H[0] = dxx * sx;
+    H[1] = dyx * sy;
+    H[2] = dxy * sx;
+    H[3] = dyy * sy;
+  }
+  // S = div N at R1 position (rx, ry) of a tile node
+  static __device__ __forceinline__ void div(const typename C::Smem &sm, const Params &P, int rx, int ry, int gxn,
+                                             int gyn, R idx_, R &Sx, R &Sy) {
+    R sx = R(0.5) * idx_, sy = R(0.5) * idx_;
+    int xa = rx + 1, xb = rx - 1, ya = ry + 1, yb = ry - 1;
+    if (EDGE) {
+      if (!P.per_x) {
+        if (gxn == 0) { xb = rx; sx = idx_; }
+        else if (gxn == P.nx - 1) { xa = rx; sx = idx_; }
+      }
+      if (!P.per_y) {
+        if (gyn == 0) { yb = ry; sy = idx_; }
+        else if (gyn == P.ny - 1) { ya = ry; sy = idx_; }
+      }
+    }
+    Sx = (sm.n[0][ry][xa] - sm.n[0][ry][xb]) * sx + (sm.n[1][ya][rx] - sm.n[1][yb][rx]) * sy;
+    Sy = (sm.n[2][ry][xa] - sm.n[2][ry][xb]) * sx + (sm.n[3][ya][rx] - sm.n[3][yb][rx]) * sy;
+  }
+};
+
+// phase 2: N over R1 from u in shared memory; N of own-tile wall nodes goes
+// to the side array
+template <class C, bool EDGE>
+__device__ __forceinline__ void phase_n(typename C::Smem &sm, const Params &P, int x0, int y0, typename C::real *bnd_out) {
+  using R = typename C::real;
+  const R lam = (R)P.lam, mu = (R)P.mu, idx_ = (R)P.inv_dx;
+  for (int e = threadIdx.x; e < C::R1W * C::R1H; e += C::NT) {
+    const int rx = e % C::R1W, ry = e / C::R1W;
+    int gx = x0 - 1 + rx, gy = y0 - 1 + ry;
+    if (EDGE && !locate(P, gx, gy)) continue;
+    R H[4], N[4];
+    Fd<C, EDGE>::grad(sm, P, rx, ry, gx, gy, idx_, H);
+    material<R>(P, lam, mu, H, N);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) sm.n[m][ry][rx] = N[m];
+    if (EDGE && bnd_out && rx >= 1 && rx <= C::TX && ry >= 1 && ry <= C::TY && x0 - 1 + rx < P.nx &&
+        y0 - 1 + ry < P.ny && on_wall(P, gx, gy))
+      store_wall_n<R>(P, bnd_out, gx, gy, N);
+  }
+}
+
+// The fused iteration on one tile.
+template <class C, bool EDGE>
+__device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, int x0, int y0) {
+  using Pr_real = typename C::real;
+  using R = Pr_real;
+  using us = typename C::us;
+  using gs = typename C::gs;
+  __shared__ typename C::Smem sm;
+  const gs *__restrict__ g = (const gs *)S.g_in;
+  gs *__restrict__ go = (gs *)S.g_out;
+  const us *__restrict__ u = (const us *)S.u_in;
+  us *__restrict__ uo = (us *)S.u_out;
+  const R *bnd = (const R *)S.b_in;
+  const int64_t k = EDGE ? (*S.kptr + S.koff) : 0;
+  const R inv = (R)ldexp(1.0, -P.gshift), scl = (R)ldexp(1.0, P.gshift);
+  const R kap = (R)P.kappa;
+  const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
+
+  // phase 1a: own nodes (keep the streamed populations)
+  R f[C::CPT][9];
+#pragma unroll
+  for (int i = 0; i < C::CPT; ++i) {
+    const int lx = tx, ly = ty + i * C::NTY;
+    const int x = x0 + lx, y = y0 + ly;
+    if (EDGE && (x >= P.nx || y >= P.ny)) continue;
+    R gxm, gym;
+    gather<typename C::PrT, EDGE>(P, g, bnd, x, y, k, inv, f[i], gxm, gym);
+    const R fx = (f[i][1] - f[i][3]) + (f[i][5] - f[i][6]) + (f[i][8] - f[i][7]);
+    const R fy = (f[i][2] - f[i][4]) + (f[i][5] - f[i][8]) + (f[i][6] - f[i][7]);
+    sm.u[ly + 2][lx + 2] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
+  }
+  // phase 1b: the 2-node frame (u only)
+  for (int e = threadIdx.x; e < C::NRING; e += C::NT) {
+    int rx, ry;
+    ring_pos<C>(e, rx, ry);
+    int x = x0 - 2 + rx, y = y0 - 2 + ry;
+    if (EDGE && !locate(P, x, y)) continue;
+    R ff[9], gxm, gym;
+    gather<typename C::PrT, EDGE>(P, g, bnd, x, y, k, inv, ff, gxm, gym);
+    const R fx = (ff[1] - ff[3]) + (ff[5] - ff[6]) + (ff[8] - ff[7]);
+    const R fy = (ff[2] - ff[4]) + (ff[5] - ff[8]) + (ff[6] - ff[7]);
+    sm.u[ry][rx] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
+  }
+  __syncthreads();
+  phase_n<C, EDGE>(sm, P, x0, y0, (R *)S.b_out);
+  __syncthreads();
+  // phase 3: source, collision, store
+  const size_t plane = (size_t)P.ny * P.pitch;
+  const R omega = (R)P.omega, sigma = (R)P.sigma, idx_ = (R)P.inv_dx;
+  const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
+#pragma unroll
+  for (int i = 0; i < C::CPT; ++i) {
+    const int lx = tx, ly = ty + i * C::NTY;
+    const int x = x0 + lx, y = y0 + ly;
+    if (EDGE && (x >= P.nx || y >= P.ny)) continue;
+    R Sx, Sy;
+    Fd<C, EDGE>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
+    Sx += sbx;
+    Sy += sby;
+    collide<R>(f[i], Sx, Sy, omega, sigma);
+    const size_t idx = (size_t)y * P.pitch + x;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[i][q], scl);
+    uo[idx] = sm.u[ly + 2][lx + 2];
+  }
+}
+
+template <class Pr, int TX, int TY, int NTY>
+struct Cfg : TileCfg<Pr, TX, TY, NTY> {
+  using PrT = Pr;
+};
+
+// interior tiles: R2 and its streaming sources lie inside, no wall, no wrap
+template <class C>
+__global__ void __launch_bounds__(C::NT) step_interior_kernel(const Params P, const StepPtrs S, int a_lo, int b_lo) {
+  step_tile<C, false>(P, S, (a_lo + blockIdx.x) * C::TX, (b_lo + blockIdx.y) * C::TY);
+}
+
+// tiles of the frame around the interior block (walls, wrap, partial tiles)
+__host__ __device__ inline void edge_tile(int e, int ntx, int a_lo, int a_hi, int b_lo, int b_hi, int &a, int &b) {
+  const int bottom = ntx * b_lo;
+  if (e < bottom) {
+    a = e % ntx;
+    b = e / ntx;
+    return;
+  }
+  e -= bottom;
+  const int side = ntx - (a_hi - a_lo);
+  const int mid = side * (b_hi - b_lo);
+  if (e < mid) {
+    b = b_lo + e / side;
+    const int c = e % side;
+    a = c < a_lo ? c : a_hi + (c - a_lo);
+    return;
+  }
+  e -= mid;
+  a = e % ntx;
+  b = b_hi + e / ntx;
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::NT) step_edge_kernel(const Params P, const StepPtrs S, int ntx, int a_lo, int a_hi,
+                                                          int b_lo, int b_hi) {
+  int a, b;
+  edge_tile(blockIdx.x, ntx, a_lo, a_hi, b_lo, b_hi, a, b);
+  step_tile<C, true>(P, S, a * C::TX, b * C::TY);
+}
+
+// interior tile range [a_lo, a_hi) x [b_lo, b_hi): R2 of the tile and the
+// streaming sources of R2 (a 3-node frame) stay clear of the walls and of the
+// lattice end.  Empty ranges are normalised to (0, 0).
+inline void interior_range(int nx, int ny, int TX, int TY, int &a_lo, int &a_hi, int &b_lo, int &b_hi) {
+  a_lo = (3 + TX - 1) / TX;
+  a_hi = (nx - 3 - TX) >= 0 ? (nx - 3 - TX) / TX + 1 : 0;
+  b_lo = (3 + TY - 1) / TY;
+  b_hi = (ny - 3 - TY) >= 0 ? (ny - 3 - TY) / TY + 1 : 0;
+  if (a_hi <= a_lo) a_lo = a_hi = 0;
+  if (b_hi <= b_lo) b_lo = b_hi = 0;
+}
+
+template <class C>
+cudaError_t launch_step(const Params &P, const StepPtrs &S, cudaStream_t st) {
+  const int ntx = (P.nx + C::TX - 1) / C::TX, nty = (P.ny + C::TY - 1) / C::TY;
+  int a_lo, a_hi, b_lo, b_hi;
+  interior_range(P.nx, P.ny, C::TX, C::TY, a_lo, a_hi, b_lo, b_hi);
+  const int ni = a_hi - a_lo, nj = b_hi - b_lo;
+  if (ni > 0 && nj > 0) step_interior_kernel<C><<<dim3(ni, nj), C::NT, 0, st>>>(P, S, a_lo, b_lo);
+  const int nedge = ntx * nty - ni * nj;
+  if (nedge > 0) step_edge_kernel<C><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ init / fields
+// u from a double field into the R2 tile (wrap or skip outside)
+template <class C>
+__device__ void load_r2_from_double(typename C::Smem &sm, const Params &P, const double *u0, int x0, int y0) {
+  for (int e = threadIdx.x; e < C::R2W * C::R2H; e += C::NT) {
+    const int rx = e % C::R2W, ry = e / C::R2W;
+    int x = x0 - 2 + rx, y = y0 - 2 + ry;
+    if (!locate(P, x, y)) continue;
+    const size_t i = (size_t)y * P.nx + x;
+    u_make(u0 ? u0[2 * i] : 0.0, u0 ? u0[2 * i + 1] : 0.0, sm.u[ry][rx]);
+  }
+}
+
+template <class C>
+__device__ void load_r2_from_state(typename C::Smem &sm, const Params &P, const typename C::us *u, int x0, int y0) {
+  for (int e = threadIdx.x; e < C::R2W * C::R2H; e += C::NT) {
+    const int rx = e % C::R2W, ry = e / C::R2W;
+    int x = x0 - 2 + rx, y = y0 - 2 + ry;
+    if (!locate(P, x, y)) continue;
+    sm.u[ry][rx] = u[(size_t)y * P.pitch + x];
+  }
+}
+
+// Alg. 1 "Initialise": r0 = -rho0 tr H0, Pi0 = Pi(H0), f0 = feq(r0, rho0 v0 - dt/2 S0, Pi0),
+// then the first collision (with S0) gives the stored g.
+template <class C>
+__global__ void __launch_bounds__(C::NT) init_kernel(const Params P, typename C::gs *g, typename C::us *u,
+                                                     typename C::real *bnd, const double *u0, const double *v0) {
+  using R = typename C::real;
+  __shared__ typename C::Smem sm;
+  const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
+  load_r2_from_double<C>(sm, P, u0, x0, y0);
+  __syncthreads();
+  phase_n<C, true>(sm, P, x0, y0, bnd);
+  __syncthreads();
+  const size_t plane = (size_t)P.ny * P.pitch;
+  const R idx_ = (R)P.inv_dx, scl = (R)ldexp(1.0, P.gshift);
+  const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
+  for (int i = 0; i < C::CPT; ++i) {
+    const int lx = tx, ly = ty + i * C::NTY, x = x0 + lx, y = y0 + ly;
+    if (x >= P.nx || y >= P.ny) continue;
+    R Sx, Sy, H[4];
+    Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
+    Sx += (R)(P.rho0 * P.body[0]);
+    Sy += (R)(P.rho0 * P.body[1]);
+    Fd<C, true>::grad(sm, P, lx + 1, ly + 1, x, y, idx_, H);
+    const size_t i0 = (size_t)y * P.nx + x;
+    const R trH = H[0] + H[3];
+    const R r0 = -(R)P.rho0 * trH;
+    // A0 = Pi(H0) / cs^2 = -rho0 (H + H^T + tr H I)
+    const R rho0 = (R)P.rho0;
+    const R Axx = -rho0 * (R(2) * H[0] + trH), Ayy = -rho0 * (R(2) * H[3] + trH), Axy = -rho0 * (H[1] + H[2]);
+    const R cr = (R)(P.c * P.inv_cs2 * P.rho0), hs = R(0.5) * (R)P.sigma;
+    const R jx = cr * (R)(v0 ? v0[2 * i0] : 0.0) - hs * Sx;
+    const R jy = cr * (R)(v0 ? v0[2 * i0 + 1] : 0.0) - hs * Sy;
+    R f[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const int e2 = ex(q) * ex(q) + ey(q) * ey(q);
+      const R rq = (e2 == 0) ? R(2) * r0 : ((e2 == 1) ? R(0.5) * r0 : -r0);
+      const R eAe = R(ex(q) * ex(q)) * Axx + R(2 * ex(q) * ey(q)) * Axy + R(ey(q) * ey(q)) * Ayy;
+      f[q] = wq<R>(q) * (rq + R(ex(q)) * jx + R(ey(q)) * jy + R(1.5) * eAe - R(0.5) * (Axx + Ayy));
+    }
+    collide<R>(f, Sx, Sy, (R)P.omega, (R)P.sigma);
+    const size_t idx = (size_t)y * P.pitch + x;
+    for (int q = 0; q < 9; ++q) gstore(g, q * plane + idx, f[q], scl);
+    u[idx] = sm.u[ly + 2][lx + 2];
+  }
+}
+
+// u, v = (c sum e g - dt/2 S) / rho0 and P = N - Pi(H) at every node
+template <class C>
+__global__ void __launch_bounds__(C::NT) fields_kernel(const Params P, const typename C::gs *g, const typename C::us *u,
+                                                       double *uo, double *vo, double *Po) {
+  using R = typename C::real;
+  __shared__ typename C::Smem sm;
+  const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
+  load_r2_from_state<C>(sm, P, u, x0, y0);
+  __syncthreads();
+  phase_n<C, true>(sm, P, x0, y0, (R *)nullptr);
+  __syncthreads();
+  const size_t plane = (size_t)P.ny * P.pitch;
+  const R idx_ = (R)P.inv_dx, inv = (R)ldexp(1.0, -P.gshift), mu = (R)P.mu;
+  const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
+  for (int i = 0; i < C::CPT; ++i) {
+    const int lx = tx, ly = ty + i * C::NTY, x = x0 + lx, y = y0 + ly;
+    if (x >= P.nx || y >= P.ny) continue;
+    const size_t o = (size_t)y * P.nx + x, idx = (size_t)y * P.pitch + x;
+    const double2 uv = u_value(sm.u[ly + 2][lx + 2]);
+    if (uo) {
+      uo[2 * o] = uv.x;
+      uo[2 * o + 1] = uv.y;
+    }
+    if (vo) {
+      R Sx, Sy;
+      Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
+      Sx += (R)(P.rho0 * P.body[0]);
+      Sy += (R)(P.rho0 * P.body[1]);
+      R m1x = 0, m1y = 0;
+      for (int q = 1; q < 9; ++q) {
+        const R gq = gload(g, q * plane + idx, inv);
+        m1x += R(ex(q)) * gq;
+        m1y += R(ey(q)) * gq;
+      }
+      const double hdt = 0.5 * P.dt;
+      vo[2 * o] = (P.c * (double)m1x - hdt * (double)Sx) / P.rho0;
+      vo[2 * o + 1] = (P.c * (double)m1y - hdt * (double)Sy) / P.rho0;
+    }
+    if (Po) {
+      R H[4];
+      Fd<C, true>::grad(sm, P, lx + 1, ly + 1, x, y, idx_, H);
+      const R trH = H[0] + H[3];
+      Po[4 * o + 0] = (double)(sm.n[0][ly + 1][lx + 1] + mu * (R(2) * H[0] + trH));
+      Po[4 * o + 1] = (double)(sm.n[1][ly + 1][lx + 1] + mu * (H[1] + H[2]));
+      Po[4 * o + 2] = (double)(sm.n[2][ly + 1][lx + 1] + mu * (H[1] + H[2]));
+      Po[4 * o + 3] = (double)(sm.n[3][ly + 1][lx + 1] + mu * (R(2) * H[3] + trH));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ monitors
+// per-block partials of: non-finite count, max |u_a|, sum c e g (x, y),
+// sum g; a warp shuffle then a shared-memory pass inside each block, and a
+// fixed-order final pass (deterministic)
+constexpr int kMonThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <class C>
+__global__ void __launch_bounds__(kMonThreads) monitor_kernel(const Params P, const typename C::gs *g,
+                                                              const typename C::us *u, double *partials) {
+  using R = typename C::real;
+  const size_t n = (size_t)P.nx * P.ny, plane = (size_t)P.ny * P.pitch;
+  const R inv = (R)ldexp(1.0, -P.gshift);
+  double bad = 0, umax = 0, mx = 0, my = 0, mass = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % P.nx), y = (int)(i / P.nx);
+    const size_t idx = (size_t)y * P.pitch + x;
+    const double2 uv = u_value(u[idx]);
+    bad += (isfinite(uv.x) ? 0.0 : 1.0) + (isfinite(uv.y) ? 0.0 : 1.0);
+    umax = fmax(umax, fmax(fabs(uv.x), fabs(uv.y)));
+    double r = 0, ax = 0, ay = 0;
+    for (int q = 0; q < 9; ++q) {
+      const double v = (double)gload(g, q * plane + idx, inv);
+      bad += isfinite(v) ? 0.0 : 1.0;
+      r += v;
+      ax += ex(q) * v;
+      ay += ey(q) * v;
+    }
+    mass += r;
+    mx += P.c * ax;
+    my += P.c * ay;
+  }
+  __shared__ double sh[5][kMonThreads / 32];
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  bad = warp_sum(bad);
+  umax = warp_max(umax);
+  mx = warp_sum(mx);
+  my = warp_sum(my);
+  mass = warp_sum(mass);
+  if (lane == 0) {
+    sh[0][w] = bad;
+    sh[1][w] = umax;
+    sh[2][w] = mx;
+    sh[3][w] = my;
+    sh[4][w] = mass;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double o[5] = {0, 0, 0, 0, 0};
+    for (int j = 0; j < kMonThreads / 32; ++j) {
+      o[0] += sh[0][j];
+      o[1] = fmax(o[1], sh[1][j]);
+      o[2] += sh[2][j];
+      o[3] += sh[3][j];
+      o[4] += sh[4][j];
+    }
+    for (int m = 0; m < 5; ++m) partials[(size_t)blockIdx.x * 5 + m] = o[m];
+  }
+}
+
+// final pass over nblocks partials; out[0..4] = bad, max|u|, momentum x, y, mass;
+// out[5] = 1 if anything was non-finite (a sticky flag: never cleared here)
+static __global__ void monitor_final_kernel(const double *partials, int nblocks, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double o[5] = {0, 0, 0, 0, 0};
+  for (int b = 0; b < nblocks; ++b) {
+    o[0] += partials[(size_t)b * 5 + 0];
+    o[1] = fmax(o[1], partials[(size_t)b * 5 + 1]);
+    o[2] += partials[(size_t)b * 5 + 2];
+    o[3] += partials[(size_t)b * 5 + 3];
+    o[4] += partials[(size_t)b * 5 + 4];
+  }
+  for (int m = 0; m < 5; ++m) out[m] = o[m];
+  if (o[0] > 0 || !isfinite(o[1])) out[5] = 1.0;
+}
+
+template <class C>
+__global__ void probe_kernel(const Params P, const typename C::us *u, const int32_t *idx, int n, double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int node = idx[i];
+  const int x = node % P.nx, y = node / P.nx;
+  const double2 uv = u_value(u[(size_t)y * P.pitch + x]);
+  out[2 * i] = uv.x;
+  out[2 * i + 1] = uv.y;
+}
+
+// ------------------------------------------------------------------ launchers
+template <class C>
+cudaError_t launch_init(const Params &P, void *g, void *u, void *b, const double *u0, const double *v0, cudaStream_t st) {
+  dim3 grid((P.nx + C::TX - 1) / C::TX, (P.ny + C::TY - 1) / C::TY);
+  init_kernel<C><<<grid, C::NT, 0, st>>>(P, (typename C::gs *)g, (typename C::us *)u, (typename C::real *)b, u0, v0);
+  return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_fields(const Params &P, const void *g, const void *u, double *uo, double *vo, double *Po,
+                          cudaStream_t st) {
+  dim3 grid((P.nx + C::TX - 1) / C::TX, (P.ny + C::TY - 1) / C::TY);
+  fields_kernel<C><<<grid, C::NT, 0, st>>>(P, (const typename C::gs *)g, (const typename C::us *)u, uo, vo, Po);
+  return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_monitor(const Params &P, const void *g, const void *u, double *partials, int nblocks, double *out6,
+                           cudaStream_t st) {
+  monitor_kernel<C><<<nblocks, kMonThreads, 0, st>>>(P, (const typename C::gs *)g, (const typename C::us *)u, partials);
+  monitor_final_kernel<<<1, 32, 0, st>>>(partials, nblocks, out6);
+  return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_probe(const Params &P, const void *u, const int32_t *idx, int n, double *out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  probe_kernel<C><<<(n + 127) / 128, 128, 0, st>>>(P, (const typename C::us *)u, idx, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbs

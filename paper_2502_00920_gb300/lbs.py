@@ -1,0 +1,288 @@
+"""ctypes binding of liblbs (include/lbs.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels.  Importing this
+module does not load the library; the first call does, and raises
+``LbsError`` if ``liblbs.so`` is missing (run ``__graft_entry__.build()``).
+
+Names follow the C ABI: ``Simulation`` wraps an ``lbs_handle``; workloads are
+described by ``paper_2502_00920_gb300.inputs.Case``.  Host field arrays are
+numpy float64 [ny, nx, 2] (u, v) and [ny, nx, 4] (P11, P12, P21, P22); device
+arrays are torch float64 CUDA tensors of the same shapes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbs.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
+PRECISION = {"fp64": 0, "fp32": 1, "fp16s": 2}
+MODEL = {"svk": 0, "nh": 1, "le": 2}
+KIND = {"periodic": 0, "dirichlet": 1, "neumann": 2}
+SHAPE = {"const": 0, "linear_ramp": 1, "sin2_ramp": 2, "half_sine": 3, "ricker": 4, "disp_ramp": 5}
+
+
+class LbsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"liblbs error {code}: {msg}")
+        self.code = code
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_double), ("tau", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("gscale_log2", ctypes.c_int32)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("E", ctypes.c_double), ("nu", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("body", ctypes.c_double * 2)]
+
+
+class EdgeC(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("shape", ctypes.c_int32), ("amp", ctypes.c_double * 2),
+                ("t0", ctypes.c_double), ("t1", ctypes.c_double), ("s", ctypes.c_double)]
+
+
+class Bcs(ctypes.Structure):
+    _fields_ = [("edge", EdgeC * 4)]
+
+
+class Monitors(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int64), ("nonfinite", ctypes.c_int64), ("max_abs_u", ctypes.c_double),
+                ("momentum", ctypes.c_double * 2), ("mass", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+# name -> (restype, argtypes); every declaration of include/lbs.h
+SIGNATURES = {
+    "lbs_create": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(Material), ctypes.POINTER(Bcs),
+                                  ctypes.POINTER(_vp)]),
+    "lbs_destroy": (ctypes.c_int, [_vp]),
+    "lbs_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "lbs_set_initial": (ctypes.c_int, [_vp, _dp, _dp]),
+    "lbs_set_initial_device": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lbs_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "lbs_sync": (ctypes.c_int, [_vp]),
+    "lbs_fields": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
+    "lbs_fields_device": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbs_probe": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _dp]),
+    "lbs_monitor": (ctypes.c_int, [_vp, ctypes.POINTER(Monitors)]),
+    "lbs_set_monitor_interval": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "lbs_set_graph_chunk": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "lbs_set_variant": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "lbs_iteration": (ctypes.c_int64, [_vp]),
+    "lbs_unstable_iteration": (ctypes.c_int64, [_vp]),
+    "lbs_cfl_warning": (ctypes.c_int, [_vp]),
+    "lbs_device_bytes": (ctypes.c_size_t, [_vp]),
+    "lbs_params": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(Material), _dp]),
+    "lbs_footprint": (ctypes.c_size_t, [ctypes.POINTER(Lattice)]),
+    "lbs_constitutive": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]),
+    "lbs_tile_variants": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, _i32p]),
+    "lbs_set_allocator": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lbs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "lbs_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load liblbs.so (once).  Raises LbsError if it has not been built."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            if not os.path.exists(LIB_PATH):
+                raise LbsError(ECUDA, f"{LIB_PATH} is missing; build it with __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def check(rc: int) -> int:
+    if rc != OK:
+        msg = lib().lbs_last_error().decode(errors="replace")
+        raise LbsError(rc, msg or lib().lbs_strerror(rc).decode())
+    return rc
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def structs(case):
+    """(Lattice, Material, Bcs) of a Case."""
+    lat = Lattice(int(case.nx), int(case.ny), float(case.dx if case.dx is not None else 1.0 / case.ny),
+                  float(case.tau), PRECISION[case.precision], int(getattr(case, "gscale_log2", 0) or 0))
+    mat = Material(MODEL[case.model], float(case.E), float(case.nu), float(case.rho0),
+                   (ctypes.c_double * 2)(float(case.body[0]), float(case.body[1])))
+    bcs = Bcs()
+    for k, e in enumerate(case.edges):
+        bcs.edge[k] = EdgeC(KIND[e.kind], SHAPE[e.shape], (ctypes.c_double * 2)(float(e.amp[0]), float(e.amp[1])),
+                            float(e.t0), float(e.t1), float(e.s))
+    return lat, mat, bcs
+
+
+def params(case) -> dict:
+    lat, mat, _ = structs(case)
+    out = np.zeros(5)
+    check(lib().lbs_params(ctypes.byref(lat), ctypes.byref(mat), _ptr(out)))
+    return dict(zip(("mu", "lam", "cs", "c", "dt"), out.tolist()))
+
+
+def footprint(case) -> int:
+    lat, _, _ = structs(case)
+    return int(lib().lbs_footprint(ctypes.byref(lat)))
+
+
+def constitutive(model: str, lam: float, mu: float, H):
+    """(P, N) of the kernels' constitutive formulas, evaluated on the host."""
+    H = np.ascontiguousarray(H, dtype=np.float64).reshape(4)
+    P = np.empty(4)
+    N = np.empty(4)
+    check(lib().lbs_constitutive(MODEL[model], float(lam), float(mu), _ptr(H), _ptr(P), _ptr(N)))
+    return P, N
+
+
+def tile_variants(precision: str = "fp32"):
+    n = ctypes.c_int32()
+    tx = (ctypes.c_int32 * 16)()
+    ty = (ctypes.c_int32 * 16)()
+    check(lib().lbs_tile_variants(PRECISION[precision], ctypes.byref(n), tx, ty))
+    return [(tx[i], ty[i]) for i in range(n.value)]
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("device fields must be contiguous float64 CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Simulation:
+    """One lattice on the GPU (an lbs_handle)."""
+
+    def __init__(self, case, u0=None, v0=None, stream=None, graph_chunk: int | None = None,
+                 monitor_interval: int | None = None, variant: int | None = None):
+        self.case = case
+        self._lat, self._mat, self._bcs = structs(case)
+        h = _vp()
+        check(lib().lbs_create(ctypes.byref(self._lat), ctypes.byref(self._mat), ctypes.byref(self._bcs),
+                               ctypes.byref(h)))
+        self._h = h
+        if stream is not None:
+            self.set_stream(stream)
+        if graph_chunk is not None:
+            check(lib().lbs_set_graph_chunk(self._h, int(graph_chunk)))
+        if monitor_interval is not None:
+            check(lib().lbs_set_monitor_interval(self._h, int(monitor_interval)))
+        if variant is not None:
+            check(lib().lbs_set_variant(self._h, int(variant)))
+        if u0 is not None or v0 is not None:
+            self.set_initial(u0, v0)
+
+    # -- life cycle
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None (own stream)."""
+        raw = getattr(stream, "cuda_stream", stream)
+        check(lib().lbs_set_stream(self._h, _vp(raw) if raw else None))
+
+    def set_initial(self, u0=None, v0=None):
+        """Host (numpy) or device (torch CUDA) initial displacement / velocity."""
+        dev = any(getattr(a, "is_cuda", False) for a in (u0, v0) if a is not None)
+        if dev:
+            check(lib().lbs_set_initial_device(self._h, _dev_ptr(u0), _dev_ptr(v0)))
+            return
+        shape = (self.case.ny, self.case.nx, 2)
+        self._u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64).reshape(shape)
+        self._v0 = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64).reshape(shape)
+        check(lib().lbs_set_initial(self._h, _ptr(self._u0) if self._u0 is not None else None,
+                                    _ptr(self._v0) if self._v0 is not None else None))
+
+    # -- stepping
+    def step(self, n: int):
+        check(lib().lbs_step(self._h, int(n)))
+
+    def sync(self):
+        check(lib().lbs_sync(self._h))
+
+    def set_graph_chunk(self, k: int):
+        check(lib().lbs_set_graph_chunk(self._h, int(k)))
+
+    def set_monitor_interval(self, m: int):
+        check(lib().lbs_set_monitor_interval(self._h, int(m)))
+
+    def set_variant(self, v: int):
+        check(lib().lbs_set_variant(self._h, int(v)))
+
+    # -- outputs
+    def fields(self, u=True, v=True, P=True):
+        ny, nx = self.case.ny, self.case.nx
+        out = [np.empty((ny, nx, w)) if want else None for want, w in ((u, 2), (v, 2), (P, 4))]
+        check(lib().lbs_fields(self._h, *[_ptr(a) if a is not None else None for a in out]))
+        return tuple(out)
+
+    def fields_device(self, u=None, v=None, P=None):
+        check(lib().lbs_fields_device(self._h, _dev_ptr(u), _dev_ptr(v), _dev_ptr(P)))
+
+    def probe(self, nodes):
+        idx = np.ascontiguousarray(nodes, dtype=np.int32).reshape(-1)
+        out = np.empty((idx.size, 2))
+        check(lib().lbs_probe(self._h, int(idx.size), idx.ctypes.data_as(_i32p), _ptr(out)))
+        return out
+
+    def monitor(self) -> dict:
+        m = Monitors()
+        check(lib().lbs_monitor(self._h, ctypes.byref(m)))
+        return dict(iteration=m.iteration, nonfinite=m.nonfinite, max_abs_u=m.max_abs_u,
+                    momentum=(m.momentum[0], m.momentum[1]), mass=m.mass)
+
+    @property
+    def iteration(self) -> int:
+        return int(lib().lbs_iteration(self._h))
+
+    @property
+    def unstable_iteration(self) -> int:
+        return int(lib().lbs_unstable_iteration(self._h))
+
+    @property
+    def cfl_warning(self) -> bool:
+        return bool(lib().lbs_cfl_warning(self._h))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().lbs_device_bytes(self._h))
