@@ -1,0 +1,301 @@
+#!/usr/bin/env python
+"""Throughput of the fused lattice update (MLUPS) on the roofline workload.
+
+Workload: a 16384 x 16384 periodic neo-Hooke lattice (E = 1, nu = 0.3,
+rho0 = 1, tau = 0.55) started from a smooth seeded random velocity field
+(correlation length 64 nodes, peak speed 0.2 c_s), FP32 storage and
+arithmetic (the displacement as a compensated float pair).  One benchmark
+step = one iteration of the method over the whole lattice (one fused kernel
+launch pair: interior tiles + frame tiles).
+
+    python bench.py [--gpus N --steps K --warmup W] [--precision fp32|fp64|fp16s]
+    python bench.py --impl reference       # the CPU oracle on the host cores
+
+N > 1 (torchrun): every rank steps its own lattice (independent replicas,
+no collective on the data path; weak scaling); the time is the maximum over
+ranks and the value the aggregate.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# algorithmic bytes per node update of the fused step: read and write of the
+# nine distributions and of the displacement record (the halo comes from L1/L2)
+BYTES_PER_NODE = {"fp64": 2 * 9 * 8 + 2 * 16, "fp32": 2 * 9 * 4 + 2 * 16, "fp16s": 2 * 9 * 2 + 2 * 16}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f16-storage/f32"}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profile_traffic(precision: str, n: int):
+    """DRAM bytes per node update of the step kernels from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        from paper_2502_00920_gb300 import build as B
+        if rec.get("source_hash") != B.source_hash():
+            return None
+        per_node = rec["bytes_per_node"].get(precision)
+        return None if per_node is None else per_node * n * n
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            self.out.flush()
+            rows = [r.split(",") for r in open(self.out.name).read().strip().splitlines() if r.strip()]
+            os.unlink(self.out.name)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(n: int, target_s: float, seed: int = 5):
+    """MLUPS of the CPU oracle on a bounded sample of the workload: the same
+    recipe (periodic neo-Hooke, seeded random velocity) on an n x n lattice,
+    stepped for about target_s seconds on all host cores."""
+    from oracle import oracle as O
+    from paper_2502_00920_gb300 import inputs as I
+    case = I.roofline(n=n, nsteps=0, precision="fp64", seed=seed)
+    v0 = I.grf_velocity(case)
+    sim = O.OracleSim(case, None, v0)
+    t0 = time.perf_counter()
+    sim.step(1)
+    t1 = time.perf_counter() - t0
+    steps = max(1, int(target_s / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": n * n * steps / dt / 1e6, "unit": "MLUPS", "cores": O.OracleSim.threads(), "kind": "oracle",
+            "sample": f"{n}x{n} periodic neo-Hooke lattice, same random-velocity recipe, {steps} iterations "
+                      f"({dt:.1f} s) after 1 untimed"}, steps, dt
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    cb, steps, dt = oracle_rate(args.ref_n, args.ref_seconds)
+    line = {"impl": "reference", "metric": "MLUPS", "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": steps, "warmup": 1, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"roofline sample {args.ref_n}x{args.ref_n} periodic neo-Hooke (oracle)",
+                       "model": "nh", "nu": 0.3, "precision": "fp64"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_precision(L, I, torch, precision, n, steps, warmup, stream, v0dev):
+    case = I.roofline(n=n, nsteps=steps, precision=precision)
+    sim = L.Simulation(case, stream=stream)
+    sim.set_initial(None, v0dev)
+    sim.step(warmup)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    sim.close()
+    bpn = BYTES_PER_NODE[precision]
+    return {"mlups": n * n / (ms * 1e-3) / 1e6, "ms_per_step": ms, "gbs": bpn * n * n / (ms * 1e-3) / 1e9,
+            "bytes_per_node": bpn}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16s"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--ref-n", type=int, default=1024)
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2502_00920_gb300 import build as B
+    B.build()
+    from paper_2502_00920_gb300 import inputs as I
+    from paper_2502_00920_gb300 import lbs as L
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("gloo")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n, K, W = args.n, args.steps, args.warmup
+    case = I.roofline(n=n, nsteps=args.e2e_steps, precision=args.precision, seed=5 + rank)
+    stream = torch.cuda.Stream(device=dev)
+    v0 = I.grf_velocity(case, device=dev)
+    sim = L.Simulation(case, stream=stream)
+    sim.set_initial(None, v0)
+    sim.step(W)
+    sim.sync()
+    launches0 = sim.launch_count
+
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        sim.step(K)
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = sim.launch_count - launches0
+    sim.sync()  # raises if a monitor saw a non-finite value
+    t = torch.tensor([ms], dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t[0])
+    cells = n * n
+    value = world * cells * K / (ms_max * 1e-3) / 1e6
+
+    # roofline of the step kernels: algorithmic bytes per launch pair / its
+    # average duration in the timed region (events on the launching stream)
+    peak, peak_kind = peaks()
+    bpn = BYTES_PER_NODE[args.precision]
+    achieved = bpn * cells / (ms / K * 1e-3) / 1e9
+    traffic = profile_traffic(args.precision, n)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "step_interior_kernel + step_edge_kernel (one iteration)",
+                "bytes_per_node": bpn, "peak_source": f"{peak_kind} hbm_gbs"}
+    clocks = clk.summary()
+    sim.close()
+
+    # end to end through the C ABI: pinned host initial velocity -> device,
+    # e2e_steps iterations, device -> pinned host u and v
+    E = args.e2e_steps
+    vh = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
+    vh.copy_(v0)
+    del v0
+    torch.cuda.empty_cache()
+    uo = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
+    vo = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
+    sim = L.Simulation(case, stream=stream)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_initial(None, vh.numpy())
+    sim.step(E)
+    sim.fields(uo.numpy(), vo.numpy(), False)
+    te = time.perf_counter() - t0
+    sim.close()
+    te_t = torch.tensor([te], dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * cells * E / float(te_t[0]) / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": vh.numel() * 8 / E, "d2h_bytes_per_step": (uo.numel() + vo.numel()) * 8 / E,
+           "job": f"set_initial(host v0) + {E} iterations + fields(host u, v)", "seconds": float(te_t[0])}
+    del vh, uo, vo
+
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        v0 = I.grf_velocity(case, device=dev)
+        for p in ("fp64", "fp32", "fp16s"):
+            variants[p] = time_precision(L, I, torch, p, n, max(10, K // 10), W, stream, v0)
+        del v0
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_rate(args.ref_n, args.ref_seconds)[0]
+    line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": f"roofline {n}x{n} periodic neo-Hooke, random initial velocity",
+                       "nx": n, "ny": n, "model": "nh", "E": 1.0, "nu": 0.3, "tau": 0.55,
+                       "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": f"state {bpn * cells / 1e9:.1f} GB per lattice, larger than L2 (no flush needed)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "precisions": variants}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

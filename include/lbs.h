@@ -183,6 +183,9 @@ int64_t lbs_unstable_iteration(const lbs_handle *h);
 int lbs_cfl_warning(const lbs_handle *h);
 /* device bytes of the handle's state */
 size_t lbs_device_bytes(const lbs_handle *h);
+/* kernels launched for this handle so far, counting every kernel node of a
+ * replayed CUDA graph */
+int64_t lbs_launch_count(const lbs_handle *h);
 
 /* ---- host utilities (no GPU needed) ------------------------------------ */
 

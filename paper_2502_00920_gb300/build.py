@@ -33,6 +33,17 @@ def _sources():
         os.path.join(HERE, "..", "include", "lbs.h")]
 
 
+def source_hash() -> str:
+    """Hash of the library sources (identifies the kernels a profile was taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for path in sorted(_sources()):
+        if os.path.exists(path):
+            h.update(os.path.basename(path).encode())
+            h.update(open(path, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(OUT):
         return False

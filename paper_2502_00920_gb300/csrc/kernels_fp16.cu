@@ -29,9 +29,19 @@ cudaError_t step(const Params &p, const StepPtrs &s, int v, cudaStream_t st) {
   }
 }
 
+int kernels_per_step(const Params &p, int v) {
+  switch (v) {
+    case 1: return step_kernel_count<V1>(p);
+    case 2: return step_kernel_count<V2>(p);
+    case 3: return step_kernel_count<V3>(p);
+    default: return step_kernel_count<V0>(p);
+  }
+}
+
 const Launchers kL = {kVariants,
                       shape,
                       step,
+                      kernels_per_step,
                       launch_init<V0>,
                       launch_fields<V0>,
                       launch_monitor<V0>,

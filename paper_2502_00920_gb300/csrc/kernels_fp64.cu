@@ -8,7 +8,7 @@ using P = F64;
 using V0 = Cfg<P, 32, 16, 8>;
 using V1 = Cfg<P, 32, 8, 8>;
 using V2 = Cfg<P, 64, 8, 4>;
-using V3 = Cfg<P, 32, 32, 8>;
+using V3 = Cfg<P, 32, 24, 8>;  // 32x32 would need 57 KB of static shared memory in FP64
 constexpr int kVariants = 4;
 
 TileShape shape(int v) {
@@ -29,9 +29,19 @@ cudaError_t step(const Params &p, const StepPtrs &s, int v, cudaStream_t st) {
   }
 }
 
+int kernels_per_step(const Params &p, int v) {
+  switch (v) {
+    case 1: return step_kernel_count<V1>(p);
+    case 2: return step_kernel_count<V2>(p);
+    case 3: return step_kernel_count<V3>(p);
+    default: return step_kernel_count<V0>(p);
+  }
+}
+
 const Launchers kL = {kVariants,
                       shape,
                       step,
+                      kernels_per_step,
                       launch_init<V0>,
                       launch_fields<V0>,
                       launch_monitor<V0>,

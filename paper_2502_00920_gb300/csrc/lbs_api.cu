@@ -228,6 +228,7 @@ struct lbs_handle {
   int graph_variant[2];
   size_t bytes;
   int cfl_warn;
+  int64_t launches;         // kernels launched for this handle
 };
 
 namespace {
@@ -297,6 +298,7 @@ int launch_monitor_async(lbs_handle *h) {
                        h->stream));
   LBS_CK(cudaMemcpyAsync(h->mon_host, h->mon_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LBS_CK(cudaEventRecord(h->mon_event, h->stream));
+  h->launches += 2;
   h->mon_pending = true;
   h->mon_k = h->k;
   return LBS_OK;
@@ -310,6 +312,7 @@ int reset_state_counters(lbs_handle *h) {
   h->next_mon = h->mon_interval;
   set_counter_kernel<<<1, 1, 0, h->stream>>>(h->kdev, 0);
   LBS_CK(cudaGetLastError());
+  h->launches += 1;
   h->kdev_value = 0;
   LBS_CK(cudaMemsetAsync(h->mon_out, 0, 6 * sizeof(double), h->stream));
   return LBS_OK;
@@ -491,6 +494,7 @@ int lbs_set_initial_device(lbs_handle *h, const double *u0, const double *v0) {
   int rc = reset_state_counters(h);
   if (rc) return rc;
   LBS_CK(h->L->init(h->P, h->g[0], h->u[0], h->b[0], u0, v0, h->stream));
+  h->launches += 1;
   return LBS_OK;
 }
 
@@ -527,13 +531,16 @@ int lbs_step(lbs_handle *h, int64_t n) {
       if (h->kdev_value != h->k) {
         set_counter_kernel<<<1, 1, 0, h->stream>>>(h->kdev, h->k);
         LBS_CK(cudaGetLastError());
+        h->launches += 1;
       }
       LBS_CK(cudaGraphLaunch(h->graph[h->parity], h->stream));
+      h->launches += (int64_t)h->graph_chunk * h->L->kernels_per_step(h->P, h->variant) + 1;
       h->k += h->graph_chunk;
       h->kdev_value = h->k;
       n -= h->graph_chunk;
     } else {
       LBS_CK(h->L->step(h->P, ptrs(h, h->parity, h->zero_dev, h->k), h->variant, h->stream));
+      h->launches += h->L->kernels_per_step(h->P, h->variant);
       h->parity ^= 1;
       h->k += 1;
       n -= 1;
@@ -558,6 +565,7 @@ int lbs_fields_device(lbs_handle *h, double *u, double *v, double *P) {
   if (!h) return fail(LBS_EINVAL, "null handle");
   if (!u && !v && !P) return LBS_OK;
   LBS_CK(h->L->fields(h->P, h->g[h->parity], h->u[h->parity], u, v, P, h->stream));
+  h->launches += 1;
   return LBS_OK;
 }
 
@@ -598,6 +606,7 @@ int lbs_probe(lbs_handle *h, int32_t n, const int32_t *idx, double *out) {
       cudaMemcpyAsync(out, dout, (size_t)n * 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     rc = fail(LBS_ECUDA, "probe failed");
+  h->launches += 1;
   dev_free(h->alloc, buf, h->stream);
   return rc;
 }
@@ -645,5 +654,6 @@ int64_t lbs_iteration(const lbs_handle *h) { return h ? h->k : -1; }
 int64_t lbs_unstable_iteration(const lbs_handle *h) { return h ? h->unstable_at : -1; }
 int lbs_cfl_warning(const lbs_handle *h) { return h ? h->cfl_warn : 0; }
 size_t lbs_device_bytes(const lbs_handle *h) { return h ? h->bytes : 0; }
+int64_t lbs_launch_count(const lbs_handle *h) { return h ? h->launches : 0; }
 
 }  // extern "C"

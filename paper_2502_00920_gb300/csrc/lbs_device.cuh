@@ -616,6 +616,15 @@ inline void interior_range(int nx, int ny, int TX, int TY, int &a_lo, int &a_hi,
 }
 
 template <class C>
+int step_kernel_count(const Params &P) {
+  const int ntx = (P.nx + C::TX - 1) / C::TX, nty = (P.ny + C::TY - 1) / C::TY;
+  int a_lo, a_hi, b_lo, b_hi;
+  interior_range(P.nx, P.ny, C::TX, C::TY, a_lo, a_hi, b_lo, b_hi);
+  const int ni = a_hi - a_lo, nj = b_hi - b_lo;
+  return (ni > 0 && nj > 0 ? 1 : 0) + (ntx * nty - ni * nj > 0 ? 1 : 0);
+}
+
+template <class C>
 cudaError_t launch_step(const Params &P, const StepPtrs &S, cudaStream_t st) {
   const int ntx = (P.nx + C::TX - 1) / C::TX, nty = (P.ny + C::TY - 1) / C::TY;
   int a_lo, a_hi, b_lo, b_hi;

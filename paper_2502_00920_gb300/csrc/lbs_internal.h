@@ -56,6 +56,7 @@ struct Launchers {
   int nvariants;
   TileShape (*shape)(int variant);
   cudaError_t (*step)(const Params &p, const StepPtrs &s, int variant, cudaStream_t st);
+  int (*kernels_per_step)(const Params &p, int variant);
   cudaError_t (*init)(const Params &p, void *g, void *u, void *b, const double *u0, const double *v0,
                       cudaStream_t st);
   cudaError_t (*fields)(const Params &p, const void *g, const void *u, double *uo, double *vo, double *Po,

@@ -84,6 +84,7 @@ SIGNATURES = {
     "lbs_unstable_iteration": (ctypes.c_int64, [_vp]),
     "lbs_cfl_warning": (ctypes.c_int, [_vp]),
     "lbs_device_bytes": (ctypes.c_size_t, [_vp]),
+    "lbs_launch_count": (ctypes.c_int64, [_vp]),
     "lbs_params": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(Material), _dp]),
     "lbs_footprint": (ctypes.c_size_t, [ctypes.POINTER(Lattice)]),
     "lbs_constitutive": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]),
@@ -251,8 +252,18 @@ class Simulation:
 
     # -- outputs
     def fields(self, u=True, v=True, P=True):
+        """Host copies of u, v, P.  Each argument is True (allocate), False
+        (skip) or a C-contiguous float64 array of the right shape to fill
+        (e.g. a view of pinned memory)."""
         ny, nx = self.case.ny, self.case.nx
-        out = [np.empty((ny, nx, w)) if want else None for want, w in ((u, 2), (v, 2), (P, 4))]
+        out = []
+        for want, w in ((u, 2), (v, 2), (P, 4)):
+            if isinstance(want, np.ndarray):
+                if want.shape != (ny, nx, w) or want.dtype != np.float64 or not want.flags.c_contiguous:
+                    raise ValueError("field buffer has the wrong shape or layout")
+                out.append(want)
+            else:
+                out.append(np.empty((ny, nx, w)) if want else None)
         check(lib().lbs_fields(self._h, *[_ptr(a) if a is not None else None for a in out]))
         return tuple(out)
 
@@ -286,3 +297,7 @@ class Simulation:
     @property
     def device_bytes(self) -> int:
         return int(lib().lbs_device_bytes(self._h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(lib().lbs_launch_count(self._h))
