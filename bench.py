@@ -176,6 +176,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -247,28 +248,34 @@ def main():
     # end to end through the C ABI: pinned host initial velocity -> device,
     # e2e_steps iterations, device -> pinned host u and v
     E = args.e2e_steps
-    vh = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
-    vh.copy_(v0)
-    del v0
-    torch.cuda.empty_cache()
-    uo = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
-    vo = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
-    sim = L.Simulation(case, stream=stream)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sim.set_initial(None, vh.numpy())
-    sim.step(E)
-    sim.fields(uo.numpy(), vo.numpy(), False)
-    te = time.perf_counter() - t0
-    sim.close()
-    te_t = torch.tensor([te], dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * cells * E / float(te_t[0]) / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": vh.numel() * 8 / E, "d2h_bytes_per_step": (uo.numel() + vo.numel()) * 8 / E,
-           "job": f"set_initial(host v0) + {E} iterations + fields(host u, v)", "seconds": float(te_t[0])}
-    del vh, uo, vo
+    e2e = None
+    if args.no_e2e:
+        E = 0
+    if E > 0:
+        vh = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
+        vh.copy_(v0)
+        del v0
+        torch.cuda.empty_cache()
+        uo = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
+        vo = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
+        sim = L.Simulation(case, stream=stream)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.set_initial(None, vh.numpy())
+        sim.step(E)
+        sim.fields(uo.numpy(), vo.numpy(), False)
+        te = time.perf_counter() - t0
+        sim.close()
+        te_t = torch.tensor([te], dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * cells * E / float(te_t[0]) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": vh.numel() * 8 / E, "d2h_bytes_per_step": (uo.numel() + vo.numel()) * 8 / E,
+               "job": f"set_initial(host v0) + {E} iterations + fields(host u, v)", "seconds": float(te_t[0])}
+        del vh, uo, vo
+    else:
+        del v0
 
     variants = None
     if not args.no_variants:

@@ -19,7 +19,7 @@
  *       P    : double [ny][nx][4]          (P11, P12, P21, P22)
  *     with P_ab = P_ab(H), H_ab = d u_a / d X_b.
  *   - Edge order in lbs_bcs: left (-x), right (+x), bottom (-y), top (+y).
- *   - Times of boundary-value shapes are iteration counts k (t_k = k dt).
+ *   - Times of boundary-value shapes are iteration counts k or times k dt.
  *   - Every function returns LBS_OK (0) or a negative LBS_E* code;
  *     lbs_last_error() gives a message for the calling thread.
  *   - The library owns all device memory of a handle (cudaMalloc, or the
@@ -59,7 +59,9 @@ enum {
 };
 enum { LBS_SVK = 0, LBS_NH = 1, LBS_LE = 2 }; /* Sect. 4; LE: lam tr(H) I + mu (H + H^T) */
 enum { LBS_PERIODIC = 0, LBS_DIRICHLET = 1, LBS_NEUMANN = 2 };
-/* time shape s(k) of a boundary value amp * s(k) */
+/* time shape s(t) of a boundary value amp * s(t); t is the iteration k or the
+ * time k dt, per edge (lbs_edge.time_unit) */
+enum { LBS_ITERATIONS = 0, LBS_TIME = 1 };
 enum {
   LBS_CONST = 0,       /* 1                                                  */
   LBS_LINEAR_RAMP = 1, /* clamp((k - t0) / (t1 - t0), 0, 1)                  */
@@ -67,7 +69,7 @@ enum {
   LBS_HALF_SINE = 3,   /* sin(pi (k - t0) / (t1 - t0)) for t0 <= k < t1, else 0 */
   LBS_RICKER = 4,      /* (1 - d^2/s) exp(-d^2 / (2 s)), d = k - t0, for k < t1 */
   LBS_DISP_RAMP = 5    /* Dirichlet only: amp is a displacement reached linearly
-                          over [t0, t1); the momentum is rho0 amp / ((t1-t0) dt)
+                          over [t0, t1); the momentum is rho0 amp / duration
                           there and 0 elsewhere                               */
 };
 
@@ -88,11 +90,12 @@ typedef struct {
 } lbs_material;
 
 typedef struct {
-  int32_t type;  /* LBS_PERIODIC | LBS_DIRICHLET (momentum j*) | LBS_NEUMANN (traction T*) */
-  int32_t shape; /* LBS_CONST ... LBS_DISP_RAMP                              */
-  double amp[2]; /* vector amplitude                                         */
-  double t0, t1; /* shape times in iterations                                */
-  double s;      /* LBS_RICKER width (iterations^2)                          */
+  int32_t type;      /* LBS_PERIODIC | LBS_DIRICHLET (momentum j*) | LBS_NEUMANN (traction T*) */
+  int32_t shape;     /* LBS_CONST ... LBS_DISP_RAMP                          */
+  double amp[2];     /* vector amplitude                                     */
+  double t0, t1;     /* shape times                                          */
+  double s;          /* LBS_RICKER width (time^2)                            */
+  int32_t time_unit; /* LBS_ITERATIONS: k; LBS_TIME: t = k dt (the paper's)  */
 } lbs_edge;
 
 typedef struct {

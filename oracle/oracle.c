@@ -31,11 +31,12 @@
  *       "extrapolated to the boundary" is the boundary node's own value; the
  *       (P + Pi(H)) used there is the array as it stands when block 2 runs,
  *       i.e. computed in block 3 of the previous iteration (or at initialisation).
- *   R8  corners: each outgoing link takes the rule of the wall it crosses; a
- *       diagonal link crossing two walls is Dirichlet if either wall is
- *       (momentum: mean of the two walls' j* when both are); at a node on two
- *       Neumann walls Pi*_xx comes from the x-wall, Pi*_yy from the y-wall and
- *       Pi*_xy is the mean of the two walls' shear entries.
+ *   R8  corners: each outgoing link takes the rule of the wall it crosses,
+ *       with the Pi* of that wall (its other diagonal entry from the node's
+ *       own moment); a diagonal link crossing two walls is Dirichlet if either
+ *       wall is (momentum: mean of the two walls' j* when both are), else its
+ *       Pi* takes Pi*_xx from the x-wall, Pi*_yy from the y-wall and the mean
+ *       of the two walls' shear entries.
  *   R9  a boundary value is evaluated at t_k = k dt of the iteration k that
  *       applies it.
  *
@@ -290,7 +291,9 @@ static void source(ora_sim *s) {
 
 void ora_load(const ora_config *cfg, int edge, long k, double out[2]) {
   const ora_edge *e = &cfg->edge[edge];
-  double t = (double)k, f = 0.0;
+  double p[5];
+  ora_params(cfg, p);
+  double t = e->time_unit ? (double)k * p[4] : (double)k, f = 0.0;
   double span = e->t1 - e->t0;
   switch (e->shape) {
     case ORA_CONST:
@@ -317,9 +320,8 @@ void ora_load(const ora_config *cfg, int edge, long k, double out[2]) {
       break;
     }
     case ORA_DISP_RAMP: {
-      double p[5];
-      ora_params(cfg, p);
-      f = (t >= e->t0 && t < e->t1) ? cfg->rho0 / (span * p[4]) : 0.0;
+      double duration = e->time_unit ? span : span * p[4];
+      f = (t >= e->t0 && t < e->t1) ? cfg->rho0 / duration : 0.0;
       break;
     }
     default:
@@ -392,6 +394,7 @@ static int validate(const ora_config *c) {
       return 0;
     if (ed->shape == ORA_RICKER && !(ed->s > 0.0)) return 0;
     if (ed->shape == ORA_DISP_RAMP && ed->type != ORA_DIRICHLET) return 0;
+    if (ed->time_unit != 0 && ed->time_unit != 1) return 0;
   }
   if (c->order != ORA_ORDER_TEXT && c->order != ORA_ORDER_LISTING) return 0;
   if ((c->edge[ORA_LEFT].type == ORA_PERIODIC) != (c->edge[ORA_RIGHT].type == ORA_PERIODIC)) return 0;
@@ -540,11 +543,6 @@ static void block2_boundaries(ora_sim *s) {
       int on_y = !s->per_y && (y == 0 || y == ny - 1);
       if (!on_x && !on_y) continue;
       long i = node(s, x, y);
-      int xw = on_x ? (x == 0 ? ORA_LEFT : ORA_RIGHT) : -1;
-      int yw = on_y ? (y == 0 ? ORA_BOTTOM : ORA_TOP) : -1;
-      /* Neumann walls this node sits on (for Pi*) */
-      int xn = (xw >= 0 && s->cfg.edge[xw].type == ORA_NEUMANN) ? xw : -1;
-      int yn = (yw >= 0 && s->cfg.edge[yw].type == ORA_NEUMANN) ? yw : -1;
       for (int q = 1; q < 9; ++q) {
         int tx = x + EX[q], ty = y + EY[q];
         int ox = !s->per_x && (tx < 0 || tx >= nx);
@@ -572,10 +570,9 @@ static void block2_boundaries(ora_sim *s) {
           out = fc - 2.0 / cs2 * W[q] * (cq[0] * js[0] + cq[1] * js[1]);
         } else {
           /* Eq. (abbcon): f_qbar = -f_q^coll + 2 w_q (r + (Pi* - r cs^2 I):(c c - cs^2 I)/(2 cs^4)) */
+          /* Pi* from the wall(s) this link crosses */
           mat2 Pis;
-          int use_x = (xn >= 0 && yn >= 0) ? xn : (wx >= 0 ? wx : -1);
-          int use_y = (xn >= 0 && yn >= 0) ? yn : (wy >= 0 ? wy : -1);
-          neumann_flux(s, i, use_x, use_y, Pis);
+          neumann_flux(s, i, wx, wy, Pis);
           double rbd = s->r[i];
           double contr = 0.0;
           for (int a = 0; a < 2; ++a)

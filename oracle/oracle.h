@@ -27,7 +27,8 @@ extern "C" {
 
 enum { ORA_SVK = 0, ORA_NH = 1, ORA_LE = 2 };
 enum { ORA_PERIODIC = 0, ORA_DIRICHLET = 1, ORA_NEUMANN = 2 };
-/* time shapes of a prescribed boundary value; times in iterations k */
+/* time shapes of a prescribed boundary value; t is the iteration k or the
+ * time k dt (ora_edge.time_unit) */
 enum {
   ORA_CONST = 0,       /* amp                                                  */
   ORA_LINEAR_RAMP = 1, /* amp * clamp((k-t0)/(t1-t0), 0, 1)                    */
@@ -35,7 +36,7 @@ enum {
   ORA_HALF_SINE = 3,   /* amp * sin(pi (k-t0)/(t1-t0)) on [t0, t1), else 0     */
   ORA_RICKER = 4,      /* amp * (1 - d^2/s) exp(-d^2/(2 s)), d = k-t0, k < t1  */
   ORA_DISP_RAMP = 5    /* Dirichlet only: amp is a displacement reached
-                          linearly over [t0, t1); value = rho0 amp/((t1-t0) dt) */
+                          linearly over [t0, t1); value = rho0 amp / duration */
 };
 /* Where the stress block sits in an iteration.  TEXT: after the displacement
  * update, so the collision at t uses S(u(t)) as the note on the source time
@@ -50,6 +51,7 @@ typedef struct {
   int shape;      /* ORA_CONST ... ORA_DISP_RAMP */
   double amp[2];
   double t0, t1, s;
+  int time_unit;  /* 0: t0, t1, s in iterations; 1: in time (t_k = k dt), s in time^2 */
 } ora_edge;
 
 typedef struct {

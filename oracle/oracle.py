@@ -41,7 +41,8 @@ def build(force: bool = False) -> str:
 
 class _Edge(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("shape", ctypes.c_int), ("amp", ctypes.c_double * 2),
-                ("t0", ctypes.c_double), ("t1", ctypes.c_double), ("s", ctypes.c_double)]
+                ("t0", ctypes.c_double), ("t1", ctypes.c_double), ("s", ctypes.c_double),
+                ("time_unit", ctypes.c_int)]
 
 
 class _Config(ctypes.Structure):
@@ -106,6 +107,7 @@ def config(case, order: str = "text") -> _Config:
         c.edge[k].shape = SHAPE[e.shape]
         c.edge[k].amp[0], c.edge[k].amp[1] = float(e.amp[0]), float(e.amp[1])
         c.edge[k].t0, c.edge[k].t1, c.edge[k].s = float(e.t0), float(e.t1), float(e.s)
+        c.edge[k].time_unit = {"steps": 0, "time": 1}[getattr(e, "unit", "steps")]
     return c
 
 

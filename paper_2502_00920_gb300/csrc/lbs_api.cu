@@ -74,6 +74,7 @@ static bool valid_edge(const lbs_edge &e) {
     return false;
   if (e.shape == LBS_RICKER && !(e.s > 0.0)) return false;
   if (e.shape == LBS_DISP_RAMP && e.type != LBS_DIRICHLET) return false;
+  if (e.time_unit != LBS_ITERATIONS && e.time_unit != LBS_TIME) return false;
   return isfinite(e.amp[0]) && isfinite(e.amp[1]);
 }
 
@@ -146,6 +147,7 @@ static Params make_params(const lbs_lattice *lat, const lbs_material *mat, const
   for (int e = 0; e < 4; ++e) {
     p.etype[e] = b->edge[e].type;
     p.eshape[e] = b->edge[e].shape;
+    p.eunit[e] = b->edge[e].time_unit;
     p.eamp[e][0] = b->edge[e].amp[0];
     p.eamp[e][1] = b->edge[e].amp[1];
     p.et0[e] = b->edge[e].t0;

@@ -170,7 +170,8 @@ __device__ __forceinline__ void material(const Params &P, R lam, R mu, const R H
 // ------------------------------------------------------------------ loads
 // prescribed boundary value amp * s(k) of edge e at iteration k
 __device__ inline void edge_value(const Params &P, int e, int64_t k, double out[2]) {
-  const double t = (double)k, t0 = P.et0[e], t1 = P.et1[e], span = t1 - t0;
+  const double t = P.eunit[e] == LBS_TIME ? (double)k * P.dt : (double)k;
+  const double t0 = P.et0[e], t1 = P.et1[e], span = t1 - t0;
   double f;
   switch (P.eshape[e]) {
     case LBS_CONST: f = 1.0; break;
@@ -186,7 +187,9 @@ __device__ inline void edge_value(const Params &P, int e, int64_t k, double out[
       f = t < t1 ? (1.0 - d * d / P.es[e]) * exp(-0.5 * d * d / P.es[e]) : 0.0;
       break;
     }
-    case LBS_DISP_RAMP: f = (t >= t0 && t < t1) ? P.rho0 / (span * P.dt) : 0.0; break;
+    case LBS_DISP_RAMP:
+      f = (t >= t0 && t < t1) ? P.rho0 / (P.eunit[e] == LBS_TIME ? span : span * P.dt) : 0.0;
+      break;
     default: f = 0.0;
   }
   out[0] = P.eamp[e][0] * f;
@@ -202,9 +205,10 @@ __device__ inline void edge_value(const Params &P, int e, int64_t k, double out[
 //   Neumann   (Eq. abbcon):  f_q = -g_qbar + 2 w_q (r + (Pi* - r cs^2 I):(c_q c_q - cs^2 I) / (2 cs^4))
 // with r and the tangential Pi entry from the node's own moments, and the
 // normal row/column of Pi* from -T* + (P + Pi(H)) N (N of this node, stored by
-// the previous iteration).  A diagonal link crossing two walls is Dirichlet if
-// either wall is (mean j* if both); at a node on two Neumann walls Pi*_xx
-// comes from the x wall, Pi*_yy from the y wall and Pi*_xy is the mean.
+// the previous iteration).  Each link uses the wall it crosses; a diagonal link
+// crossing two walls is Dirichlet if either wall is (mean j* if both), else
+// its Pi* takes Pi*_xx from the x wall, Pi*_yy from the y wall and the mean of
+// the two shear entries.
 template <class R>
 __device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t k, const R g0[9], unsigned mask,
                            R f[9]) {
@@ -223,28 +227,26 @@ __device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t 
     mxy += R(ex(q) * ey(q)) * g0[q];
     myy += R(ey(q) * ey(q)) * g0[q];
   }
-  R Axx = R(3) * mxx, Axy = R(3) * mxy, Ayy = R(3) * myy;
-  if (xn || yn) {
-    R axy_x = 0, axy_y = 0;
-    if (xn) {
-      const R *Nn = bnd + ((size_t)xw * P.blen + y) * 4;  // N11, N12, N21, N22
-      double T[2];
-      edge_value(P, xw, k, T);
-      const R s = (xw == kRight) ? R(1) : R(-1);
-      Axx = (Nn[0] - s * (R)T[0]) * ics2;
-      axy_x = (Nn[2] - s * (R)T[1]) * ics2;
-    }
-    if (yn) {
-      const R *Nn = bnd + ((size_t)yw * P.blen + x) * 4;
-      double T[2];
-      edge_value(P, yw, k, T);
-      const R s = (yw == kTop) ? R(1) : R(-1);
-      Ayy = (Nn[3] - s * (R)T[1]) * ics2;
-      axy_y = (Nn[1] - s * (R)T[0]) * ics2;
-    }
-    Axy = (xn && yn) ? R(0.5) * (axy_x + axy_y) : (xn ? axy_x : axy_y);
+  // Pi*/cs^2 pieces: the node's own moment (entries extrapolated to the wall)
+  // and the normal column of each Neumann wall the node sits on
+  const R Axx_o = R(3) * mxx, Axy_o = R(3) * mxy, Ayy_o = R(3) * myy;
+  R Axx_x = 0, axy_x = 0, Ayy_y = 0, axy_y = 0;
+  if (xn) {
+    const R *Nn = bnd + ((size_t)xw * P.blen + y) * 4;  // N11, N12, N21, N22
+    double T[2];
+    edge_value(P, xw, k, T);
+    const R s = (xw == kRight) ? R(1) : R(-1);
+    Axx_x = (Nn[0] - s * (R)T[0]) * ics2;
+    axy_x = (Nn[2] - s * (R)T[1]) * ics2;
   }
-  const R trA = Axx + Ayy;
+  if (yn) {
+    const R *Nn = bnd + ((size_t)yw * P.blen + x) * 4;
+    double T[2];
+    edge_value(P, yw, k, T);
+    const R s = (yw == kTop) ? R(1) : R(-1);
+    Ayy_y = (Nn[3] - s * (R)T[1]) * ics2;
+    axy_y = (Nn[1] - s * (R)T[0]) * ics2;
+  }
   const R cj = (R)(P.c * P.inv_cs2);
 #pragma unroll
   for (int q = 1; q < 9; ++q) {
@@ -267,9 +269,13 @@ __device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t 
       }
       f[q] = g0[qb] + R(2) * wq<R>(q) * cj * (R(ex(q)) * (R)js[0] + R(ey(q)) * (R)js[1]);
     } else {
+      // Pi* of the wall(s) this link crosses
+      const R Axx = ox ? Axx_x : Axx_o;
+      const R Ayy = oy ? Ayy_y : Ayy_o;
+      const R Axy = (ox && oy) ? R(0.5) * (axy_x + axy_y) : (ox ? axy_x : axy_y);
       const R e2 = R(ex(q) * ex(q) + ey(q) * ey(q));
       const R eAe = R(ex(q) * ex(q)) * Axx + R(2 * ex(q) * ey(q)) * Axy + R(ey(q) * ey(q)) * Ayy;
-      f[q] = -g0[qb] + wq<R>(q) * (R(4) * r - R(3) * r * e2 + R(3) * eAe - trA);
+      f[q] = -g0[qb] + wq<R>(q) * (R(4) * r - R(3) * r * e2 + R(3) * eAe - (Axx + Ayy));
     }
   }
 }
@@ -513,13 +519,16 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
   const R kap = (R)P.kappa;
   const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
 
-  // phase 1a: own nodes (keep the streamed populations)
+  // phase 1a: own nodes (keep the streamed populations).  In a tile that
+  // overhangs the end of a periodic axis, the positions past the end are
+  // wrapped neighbours that the stencils of the last nodes read: their u is
+  // computed here too, but they are not stored.
   R f[C::CPT][9];
 #pragma unroll
   for (int i = 0; i < C::CPT; ++i) {
     const int lx = tx, ly = ty + i * C::NTY;
-    const int x = x0 + lx, y = y0 + ly;
-    if (EDGE && (x >= P.nx || y >= P.ny)) continue;
+    int x = x0 + lx, y = y0 + ly;
+    if (EDGE && !locate(P, x, y)) continue;
     R gxm, gym;
     gather<typename C::PrT, EDGE>(P, g, bnd, x, y, k, inv, f[i], gxm, gym);
     const R fx = (f[i][1] - f[i][3]) + (f[i][5] - f[i][6]) + (f[i][8] - f[i][7]);

@@ -20,7 +20,7 @@ struct Params {
   int blen;           // entries per edge of the boundary side array
   int model;
   int gshift;         // FP16S: stored g = g * 2^gshift
-  int etype[4], eshape[4];
+  int etype[4], eshape[4], eunit[4];
   double eamp[4][2], et0[4], et1[4], es[4];
   double mu, lam, rho0, cs, c, dt, dx, tau;
   double body[2];

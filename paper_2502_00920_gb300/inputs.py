@@ -40,6 +40,7 @@ class Edge:
     t0: float = 0.0
     t1: float = 1.0
     s: float = 1.0
+    unit: str = "steps"  # "steps": times are iterations k; "time": t = k dt
 
 
 PERIODIC = Edge("periodic")
@@ -130,6 +131,42 @@ def shear_speed(case: Case) -> float:
     scale synthetic initial velocities."""
     mu = case.E / (2.0 * (1.0 + case.nu))
     return math.sqrt(mu / case.rho0)
+
+
+# --------------------------------------------------------------------------
+# the paper's own examples (Sect. 4), with times in the paper's time unit
+
+def paper_tension(model: str = "nh", nu: float = 0.3, n: int = 40, precision: str = "fp64") -> Case:
+    """Sect. 4.1: 1L x 1L, traction sigma* = alpha sin^2(pi t / 4) for t < 2,
+    then alpha, on top (+) and bottom (-); left and right free; alpha = 0.175
+    (SVK) or 0.35 (neo-Hooke); dx = 1/n (0.025 for n = 40)."""
+    alpha = 0.175 if model == "svk" else 0.35
+    top = Edge("neumann", "sin2_ramp", (0.0, alpha), 0.0, 2.0, unit="time")
+    bottom = Edge("neumann", "sin2_ramp", (0.0, -alpha), 0.0, 2.0, unit="time")
+    return Case(f"paper_tension_{model}_nu{nu}_{n}", n, n, 0, model=model, nu=nu, dx=1.0 / n,
+                edges=(FREE, FREE, bottom, top), precision=precision)
+
+
+def paper_shear(model: str = "nh", nu: float = 0.3, n: int = 40, precision: str = "fp64") -> Case:
+    """Sect. 4.2: bottom clamped, top momentum j* = alpha sin(pi t / 2) for
+    t < 2, then 0; alpha = 0.03 (SVK) or 0.1 (neo-Hooke)."""
+    alpha = 0.03 if model == "svk" else 0.1
+    top = Edge("dirichlet", "half_sine", (alpha, 0.0), 0.0, 2.0, unit="time")
+    return Case(f"paper_shear_{model}_nu{nu}_{n}", n, n, 0, model=model, nu=nu, dx=1.0 / n,
+                edges=(FREE, FREE, CLAMPED, top), precision=precision)
+
+
+def paper_wave(tau: float = 0.55, n: int = 40, precision: str = "fp64") -> Case:
+    """Sect. 4.3: 4L x 1L beam, left end clamped, tangential Ricker traction on
+    the right end (alpha = 0.15, s = 0.215, t0 = 1, free for t > 2), neo-Hooke
+    nu = 0.2.  The garbled prefactor of Eq. ricker is read as
+    2 / (sqrt(3 sigma) pi^(1/4)) with sigma = sqrt(s) and folded into amp."""
+    s_ = 0.215
+    sigma = math.sqrt(s_)
+    amp = 0.15 * 2.0 / (math.sqrt(3.0 * sigma) * math.pi ** 0.25)
+    right = Edge("neumann", "ricker", (0.0, amp), 1.0, 2.0, s_, unit="time")
+    return Case(f"paper_wave_tau{tau}", 4 * n, n, 0, model="nh", nu=0.2, dx=1.0 / n, tau=tau,
+                edges=(CLAMPED, right, FREE, FREE), precision=precision)
 
 
 # --------------------------------------------------------------------------

@@ -26,6 +26,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3
 PRECISION = {"fp64": 0, "fp32": 1, "fp16s": 2}
 MODEL = {"svk": 0, "nh": 1, "le": 2}
 KIND = {"periodic": 0, "dirichlet": 1, "neumann": 2}
+UNIT = {"steps": 0, "time": 1}
 SHAPE = {"const": 0, "linear_ramp": 1, "sin2_ramp": 2, "half_sine": 3, "ricker": 4, "disp_ramp": 5}
 
 
@@ -47,7 +48,8 @@ class Material(ctypes.Structure):
 
 class EdgeC(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int32), ("shape", ctypes.c_int32), ("amp", ctypes.c_double * 2),
-                ("t0", ctypes.c_double), ("t1", ctypes.c_double), ("s", ctypes.c_double)]
+                ("t0", ctypes.c_double), ("t1", ctypes.c_double), ("s", ctypes.c_double),
+                ("time_unit", ctypes.c_int32)]
 
 
 class Bcs(ctypes.Structure):
@@ -131,7 +133,7 @@ def structs(case):
     bcs = Bcs()
     for k, e in enumerate(case.edges):
         bcs.edge[k] = EdgeC(KIND[e.kind], SHAPE[e.shape], (ctypes.c_double * 2)(float(e.amp[0]), float(e.amp[1])),
-                            float(e.t0), float(e.t1), float(e.s))
+                            float(e.t0), float(e.t1), float(e.s), UNIT[getattr(e, "unit", "steps")])
     return lat, mat, bcs
 
 

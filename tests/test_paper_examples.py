@@ -1,0 +1,39 @@
+"""The paper's own examples (Sect. 4) on the oracle, over the horizons the paper
+reports: uniaxial tension and simple shear to t = 2.2 for every Poisson ratio
+of Tab. 2/3, and the bending wave to t = 12 for every relaxation time of
+Fig. wave.  The paper runs all of them without blow-up; the per-link corner
+rule (a link takes the Neumann flux of the wall it crosses) is the reading
+under which the oracle does too.  The finite-element reference solutions of
+Tab. 2/3 are not available, so only boundedness and symmetry are checked."""
+import numpy as np
+import pytest
+
+from paper_2502_00920_gb300 import inputs as I
+
+
+def run_to(O, case, T):
+    dt = O.params(case)["dt"]
+    s = O.OracleSim(case)
+    s.step(int(round(T / dt)))
+    return s.fields()
+
+
+@pytest.mark.parametrize("model,nu", [("svk", nu) for nu in (0.0, 0.1, 0.2, 0.25, 0.3)] +
+                         [("nh", nu) for nu in (-0.1, 0.0, 0.1, 0.2, 0.25, 0.3)])
+def test_paper_tension_and_shear_stay_bounded(oracle_mod, model, nu):
+    u, v, P = run_to(oracle_mod, I.paper_tension(model, nu), 2.2)
+    assert np.isfinite(u).all() and np.abs(u).max() < 0.6
+    # loaded symmetrically at top and bottom: u_y odd, u_x even about the mid-line
+    np.testing.assert_allclose(u[::-1, :, 1], -u[:, :, 1], atol=1e-10)
+    np.testing.assert_allclose(u[:, ::-1, 0], -u[:, :, 0], atol=1e-10)
+    assert u[-1, :, 1].mean() > 0.0
+    u, v, P = run_to(oracle_mod, I.paper_shear(model, nu), 2.2)
+    assert np.isfinite(u).all() and np.abs(u).max() < 0.2
+    assert u[-1, :, 0].mean() > 0.0
+
+
+@pytest.mark.parametrize("tau", [0.54, 0.55, 0.57, 0.59])
+def test_paper_bending_wave_stays_bounded(oracle_mod, tau):
+    u, v, P = run_to(oracle_mod, I.paper_wave(tau), 12.0)
+    assert np.isfinite(u).all() and np.abs(u).max() < 0.6
+    assert np.abs(u[:, 0]).max() == 0.0 or np.abs(u[:, 0]).max() < 0.05  # clamped end stays near rest

@@ -30,6 +30,29 @@ def L():
     return lbs
 
 
+ERRORS = {}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _error_report():
+    """Write every measured error to gpurun_out/parity_errors.json (or the
+    directory in LBS_ERROR_REPORT) for the record."""
+    yield
+    import json
+    import os
+    out = os.environ.get("LBS_ERROR_REPORT", "gpurun_out")
+    try:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "parity_errors.json"), "w") as f:
+            json.dump(ERRORS, f, indent=1, sort_keys=True)
+    except OSError:
+        pass
+
+
+def record(key, **errs):
+    ERRORS[key] = {k: float(v) for k, v in errs.items()}
+
+
 def rel(a, b):
     d = np.abs(b).max()
     return np.abs(a - b).max() / (d if d > 0 else 1.0)
@@ -83,6 +106,7 @@ def test_fp64_matches_oracle(L, oracle_mod, name):
     u0, v0 = rnd(case) if random_init else (None, None)
     u, v, P = run_gpu(L, case, steps, u0, v0)
     ur, vr, Pr = run_oracle(oracle_mod, case, steps, u0, v0)
+    record(f"fp64/{name}", u=rel(u, ur), v=rel(v, vr), P=rel(P, Pr))
     assert np.isfinite(ur).all() and np.abs(ur).max() > 1e-6
     assert rel(u, ur) <= TOL["fp64"], rel(u, ur)
     assert rel(v, vr) <= TOL["fp64"], rel(v, vr)
@@ -97,6 +121,7 @@ def test_reduced_precision_matches_oracle(L, oracle_mod, name, precision):
     u0, v0 = rnd(case) if random_init else (None, None)
     u, v, P = run_gpu(L, case.replace(precision=precision), steps, u0, v0)
     ur, vr, Pr = run_oracle(oracle_mod, case, steps, u0, v0)
+    record(f"{precision}/{name}", u=rel(u, ur), v=rel(v, vr), P=rel(P, Pr))
     assert rel(u, ur) <= TOL[precision], rel(u, ur)
 
 
@@ -258,6 +283,7 @@ def test_roofline_lattice_16384_windows(L, oracle_mod, precision):
     case = I.roofline(n=16384, nsteps=6)
     starts = [(0, 0), (16384 - 16, 100), (8000, 16384 - 20), (12345, 6789)]
     errs = light_cone_windows(L, oracle_mod, case, 6, starts, precision=precision, graph_chunk=64)
+    record(f"{precision}/roofline_16384_windows", u=max(e[0] for e in errs), v=max(e[1] for e in errs))
     for eu, ev in errs:
         assert eu <= TOL[precision], errs
         if precision == "fp64":
@@ -272,6 +298,7 @@ def test_shear_256_sweep(L, oracle_mod):
         ur, vr, Pr = run_oracle(oracle_mod, case, 400)
         if not np.isfinite(ur).all():
             continue
+        record(f"fp64/shear_256_nu{nu}", u=rel(u, ur), v=rel(v, vr), P=rel(P, Pr))
         assert rel(u, ur) <= 1e-12 and rel(v, vr) <= 1e-12, (nu, rel(u, ur))
 
 
@@ -280,8 +307,10 @@ def test_cantilever_4096x256(L, oracle_mod):
     case = I.cantilever(4096, 256, 0, precision="fp64")
     u, v, P = run_gpu(L, case, 250)
     ur, vr, Pr = run_oracle(oracle_mod, case, 250)
-    assert rel(u, ur) <= 1e-12 and rel(v, vr) <= 1e-12
     u32 = run_gpu(L, case.replace(precision="fp32"), 250)[0]
+    record("fp64/cantilever_4096x256", u=rel(u, ur), v=rel(v, vr), P=rel(P, Pr))
+    record("fp32/cantilever_4096x256", u=rel(u32, ur))
+    assert rel(u, ur) <= 1e-12 and rel(v, vr) <= 1e-12
     assert rel(u32, ur) <= 1e-5
 
 
