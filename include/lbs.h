@@ -148,7 +148,9 @@ int lbs_set_initial_device(lbs_handle *h, const double *u0, const double *v0);
 int lbs_step(lbs_handle *h, int64_t n);
 
 /* Wait for the handle's work; LBS_EUNSTABLE if a monitor found a
- * non-finite value (lbs_unstable_iteration tells where). */
+ * non-finite value (lbs_unstable_iteration tells where), LBS_ETIMEOUT if a
+ * kernel gave up waiting for its tile copies (bounded wait; the state is then
+ * not advanced for the affected tiles). */
 int lbs_sync(lbs_handle *h);
 
 /* Fields at the current iteration into caller-owned HOST buffers (any may be
@@ -175,8 +177,8 @@ int lbs_set_monitor_interval(lbs_handle *h, int64_t m);
  * Default 64. */
 int lbs_set_graph_chunk(lbs_handle *h, int32_t k);
 
-/* Kernel tile variant (0 = default, else an index from lbs_tile_variants);
- * used by the autotuner. */
+/* Kernel tile variant (an index from lbs_tile_variants).  Each precision has a
+ * default (the fastest on a large lattice); lbs_autotune picks per lattice. */
 int lbs_set_variant(lbs_handle *h, int32_t variant);
 
 int64_t lbs_iteration(const lbs_handle *h);
@@ -207,6 +209,32 @@ int lbs_constitutive(int32_t model, double lam, double mu, const double H[4], do
 /* Number of tile variants compiled for a precision, and their shapes
  * (cells along x and y per thread block). */
 int lbs_tile_variants(int32_t precision, int32_t *count, int32_t *tx, int32_t *ty);
+
+/* 1 if a tile variant stages its interior tiles in shared memory with TMA
+ * (cp.async.bulk.tensor), 0 if it reads global memory directly; negative
+ * LBS_EINVAL for an unknown precision or variant. */
+int lbs_tile_variant_kind(int32_t precision, int32_t variant);
+
+/* ---- autotuner ---------------------------------------------------------- */
+
+/* Time every tile variant (lbs_tile_variants) for this configuration on a
+ * scratch lattice with the same material, edges and precision and at most
+ * 4096 x 4096 nodes (direct launches, CUDA events, `steps` iterations after
+ * two untimed ones) and return the fastest in *best.  ms, if not NULL,
+ * receives the time per iteration of each variant.  Results are cached per
+ * (nx, ny, precision, model, periodic axes) for the life of the process;
+ * a cached configuration is not timed again.  Allocates a scratch lattice. */
+int lbs_autotune(const lbs_lattice *lat, const lbs_material *mat, const lbs_bcs *bcs, int32_t steps, int32_t *best,
+                 float *ms);
+
+/* Tune (or look up) the handle's configuration and select the winner. */
+int lbs_autotune_handle(lbs_handle *h, int32_t steps);
+
+/* Save / load the tuning cache as JSON lines
+ * {"nx": .., "ny": .., "precision": .., "model": .., "per_x": .., "per_y": .., "variant": .., "ms": [..]}.
+ * Loading merges into the cache (unknown variants are ignored). */
+int lbs_autotune_save(const char *path);
+int lbs_autotune_load(const char *path);
 
 /* Install the device allocator used for handle state (NULL, NULL restores
  * cudaMalloc/cudaFree).  alloc(bytes, stream, ctx) returns a device pointer

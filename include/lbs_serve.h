@@ -1,0 +1,98 @@
+/*
+ * lbs_serve.h - continuous-batching server of liblbs (see lbs.h).
+ *
+ * Many independent simulations (lattices of different sizes, materials and
+ * boundary loads; each one Algorithm 1 of the paper from rest for a given
+ * number of iterations) share one GPU.  A worker thread admits queued
+ * requests while their device footprint (lbs_footprint) fits the HBM budget,
+ * keeps the admitted lattices' state resident, and advances all of them
+ * together: every iteration is one launch of a batched kernel that walks a
+ * tile table spanning all resident lattices (interior tiles, then frame
+ * tiles) and one launch that advances their iteration counters.  The worker
+ * runs `chunk` iterations between scheduling points; a lattice that reaches
+ * its iteration count stops (its tiles return at once), is checked for
+ * non-finite values, has u, v and P copied to host memory owned by the server
+ * and its device memory released, after which queued requests are admitted.
+ * Each lattice computes exactly what lbs_step computes for it alone.
+ *
+ * The server owns its device memory and its results until lbs_result hands
+ * them over.  All functions are thread-safe.
+ */
+#ifndef LBS_SERVE_H
+#define LBS_SERVE_H
+
+#include "lbs.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbs_server lbs_server;
+
+typedef struct {
+  size_t hbm_budget;     /* device bytes for resident lattices (0: 80 % of free memory) */
+  int32_t precision;     /* storage precision of every request (LBS_FP32 ...)          */
+  int32_t chunk;         /* iterations between scheduling points (0: 64)               */
+  int32_t max_resident;  /* cap on resident lattices (0: none)                          */
+  int32_t queue_limit;   /* lbs_submit returns LBS_EBUSY beyond this many queued (0: none) */
+} lbs_server_config;
+
+enum { LBS_TICKET_QUEUED = 0, LBS_TICKET_RUNNING = 1, LBS_TICKET_DONE = 2, LBS_TICKET_FAILED = 3 };
+
+typedef struct {
+  int32_t state;       /* LBS_TICKET_*                                           */
+  int32_t error;       /* LBS_OK, or why it failed (LBS_EUNSTABLE, LBS_ENOMEM ...) */
+  int64_t iterations;  /* iterations completed                                    */
+  int64_t nsteps;      /* iterations requested                                    */
+  int32_t nx, ny;
+  double t_submit;     /* seconds on the server clock (0 = server creation)       */
+  double t_admit;      /* admission to the GPU (-1 while queued)                  */
+  double t_done;       /* completion (-1 until done or failed)                    */
+  size_t device_bytes; /* footprint while resident                                */
+} lbs_ticket_info;
+
+typedef struct {
+  int64_t submitted, completed, failed, queued, resident;
+  int64_t node_updates;   /* nodes x iterations of finished lattices          */
+  double busy_seconds;    /* wall time with at least one resident lattice      */
+  size_t bytes_in_use;    /* device bytes of resident lattices                 */
+  size_t hbm_budget;
+  int64_t launches;       /* kernels launched by the worker                    */
+} lbs_server_stats;
+
+/* Start a server on the current CUDA device.  Errors: LBS_EINVAL (bad
+ * precision or negative sizes), LBS_ECUDA. */
+int lbs_server_create(const lbs_server_config *cfg, lbs_server **out);
+
+/* Queue a simulation from rest for nsteps iterations.  The precision of the
+ * lattice is replaced by the server's.  *ticket identifies it.  Errors:
+ * LBS_EINVAL (as lbs_create), LBS_ENOMEM (larger than the whole budget),
+ * LBS_EBUSY (queue limit). */
+int lbs_submit(lbs_server *s, const lbs_lattice *lat, const lbs_material *mat, const lbs_bcs *bcs, int64_t nsteps,
+               uint64_t *ticket);
+
+/* Status of a ticket.  LBS_ENOTFOUND for unknown or already collected tickets. */
+int lbs_poll(lbs_server *s, uint64_t ticket, lbs_ticket_info *info);
+
+/* Block until the ticket is done or failed, at most timeout_s seconds
+ * (< 0: no limit).  LBS_ETIMEOUT if the time ran out. */
+int lbs_wait(lbs_server *s, uint64_t ticket, double timeout_s);
+
+/* Copy the final fields of a finished ticket into caller-owned host buffers
+ * (layouts as lbs_fields; any may be NULL) and forget the ticket.  Returns
+ * the ticket's error code for a failed ticket (its fields as they stood when
+ * it stopped are still copied), LBS_EBUSY if it is not finished. */
+int lbs_result(lbs_server *s, uint64_t ticket, double *u, double *v, double *P);
+
+/* Block until every submitted ticket is done or failed (timeout as lbs_wait). */
+int lbs_server_drain(lbs_server *s, double timeout_s);
+
+int lbs_server_get_stats(lbs_server *s, lbs_server_stats *out);
+
+/* Stop the worker (after the iteration chunk in flight), free everything. */
+int lbs_server_destroy(lbs_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBS_SERVE_H */

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall"]
-UNITS = ["lbs_api.cu", "kernels_fp64.cu", "kernels_fp32.cu", "kernels_fp16.cu"]
+UNITS = ["lbs_api.cu", "lbs_autotune.cu", "lbs_serve.cu", "kernels_fp64.cu", "kernels_fp32.cu", "kernels_fp16.cu"]
 
 
 def nvcc() -> str:
@@ -29,8 +29,9 @@ def nvcc() -> str:
 
 
 def _sources():
+    inc = os.path.join(HERE, "..", "include")
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))] + [
-        os.path.join(HERE, "..", "include", "lbs.h")]
+        os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
 
 
 def source_hash() -> str:

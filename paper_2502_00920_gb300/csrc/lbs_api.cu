@@ -22,11 +22,7 @@ static lbs_alloc_fn g_alloc = nullptr;
 static lbs_free_fn g_free = nullptr;
 static void *g_alloc_ctx = nullptr;
 
-struct Allocator {
-  lbs_alloc_fn alloc;
-  lbs_free_fn release;
-  void *ctx;
-};
+
 
 static Allocator current_allocator() {
   std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -191,7 +187,7 @@ static Sizes sizes_of(const Params &p, const Launchers &L) {
   s.g = (size_t)9 * p.ny * p.pitch * L.g_elem;
   s.u = (size_t)p.ny * p.pitch * L.u_elem;
   s.b = (size_t)4 * p.blen * 4 * L.b_elem;
-  s.mon = (size_t)monitor_blocks(p) * 5 * sizeof(double) + 8 * sizeof(double) + 2 * sizeof(int64_t);
+  s.mon = (size_t)monitor_blocks(p) * 5 * sizeof(double) + 8 * sizeof(double) + 3 * sizeof(int64_t);
   return s;
 }
 
@@ -202,36 +198,7 @@ __global__ void add_counter_kernel(int64_t *k, int64_t d) { *k += d; }
 
 using namespace lbs;
 
-struct lbs_handle {
-  Params P;
-  int precision;
-  const Launchers *L;
-  int variant;
-  Allocator alloc;
-  cudaStream_t own_stream;
-  cudaStream_t stream;
-  void *g[2], *u[2], *b[2];
-  void *mon_block;          // partials, out[8], counters
-  double *mon_partials;
-  double *mon_out;          // device: bad, max|u|, mx, my, mass, flag
-  int64_t *kdev;            // device iteration base used by graph replays
-  int64_t *zero_dev;        // device constant 0 (direct launches)
-  double *mon_host;         // pinned copy of mon_out
-  cudaEvent_t mon_event;
-  bool mon_pending;
-  int64_t mon_k;            // iteration of the pending monitor
-  int64_t mon_interval, next_mon;
-  int parity;               // the current state sits in buffers [parity]
-  int64_t k;                // iteration counter
-  int64_t kdev_value;       // value held by *kdev (host mirror)
-  int64_t unstable_at;
-  int graph_chunk;
-  cudaGraphExec_t graph[2];
-  int graph_variant[2];
-  size_t bytes;
-  int cfl_warn;
-  int64_t launches;         // kernels launched for this handle
-};
+
 
 namespace {
 
@@ -245,6 +212,9 @@ StepPtrs ptrs(const lbs_handle *h, int parity, const int64_t *kptr, int64_t koff
   s.b_out = h->b[parity ^ 1];
   s.kptr = kptr;
   s.koff = koff;
+  s.tm_g = h->tma ? (const void *)&h->tm_g[parity] : nullptr;
+  s.tm_u = h->tma ? (const void *)&h->tm_u[parity] : nullptr;
+  s.err = h->errdev;
   return s;
 }
 
@@ -303,6 +273,17 @@ int launch_monitor_async(lbs_handle *h) {
   h->launches += 2;
   h->mon_pending = true;
   h->mon_k = h->k;
+  return LBS_OK;
+}
+
+// select a tile variant; TMA variants get their descriptors built here
+int select_variant(lbs_handle *h, int variant) {
+  bool tma = h->L->tma_maps(h->P, variant, h->g[0], h->u[0], &h->tm_g[0], &h->tm_u[0]);
+  if (tma) tma = h->L->tma_maps(h->P, variant, h->g[1], h->u[1], &h->tm_g[1], &h->tm_u[1]);
+  if (!tma && variant == h->L->tma_index)
+    return fail(LBS_ECUDA, "TMA descriptors could not be built for tile variant " + std::to_string(variant));
+  h->tma = tma;
+  h->variant = variant;
   return LBS_OK;
 }
 
@@ -381,6 +362,13 @@ int lbs_constitutive(int32_t model, double lam, double mu, const double H[4], do
   return LBS_OK;
 }
 
+int lbs_tile_variant_kind(int32_t precision, int32_t variant) {
+  if (precision < LBS_FP64 || precision > LBS_FP16S) return fail(LBS_EINVAL, "unknown precision");
+  const Launchers &L = launchers_for(precision);
+  if (variant < 0 || variant >= L.nvariants) return fail(LBS_EINVAL, "unknown tile variant");
+  return variant == L.tma_index ? 1 : 0;
+}
+
 int lbs_tile_variants(int32_t precision, int32_t *count, int32_t *tx, int32_t *ty) {
   if (precision < LBS_FP64 || precision > LBS_FP16S) return fail(LBS_EINVAL, "unknown precision");
   const Launchers &L = launchers_for(precision);
@@ -401,9 +389,17 @@ int lbs_create(const lbs_lattice *lat, const lbs_material *mat, const lbs_bcs *b
   lbs_handle *h = new (std::nothrow) lbs_handle();
   if (!h) return fail(LBS_ENOMEM, "host allocation");
   h->P = make_params(lat, mat, bcs);
+  h->lat = *lat;
+  h->mat = *mat;
+  if (bcs) {
+    h->bcs = *bcs;
+  } else {
+    memset(&h->bcs, 0, sizeof(h->bcs));
+    for (int e = 0; e < 4; ++e) h->bcs.edge[e].type = LBS_NEUMANN;
+  }
   h->precision = lat->precision;
   h->L = &launchers_for(lat->precision);
-  h->variant = 0;
+  h->variant = -1;
   h->alloc = current_allocator();
   h->mon_interval = 1000;
   h->graph_chunk = 64;
@@ -445,9 +441,10 @@ int lbs_create(const lbs_lattice *lat, const lbs_material *mat, const lbs_bcs *b
   h->mon_out = (double *)(mb + (size_t)monitor_blocks(h->P) * 5 * sizeof(double));
   h->kdev = (int64_t *)(h->mon_out + 8);
   h->zero_dev = h->kdev + 1;
+  h->errdev = (int *)(h->kdev + 2);
   h->bytes = 2 * (s.g + s.u + s.b) + s.mon;
-  rc = LBS_OK;
-  if (cudaMemsetAsync(h->zero_dev, 0, sizeof(int64_t), h->stream) != cudaSuccess) rc = LBS_ECUDA;
+  rc = select_variant(h, h->L->default_variant);
+  if (!rc && cudaMemsetAsync(h->zero_dev, 0, 2 * sizeof(int64_t), h->stream) != cudaSuccess) rc = LBS_ECUDA;
   if (!rc) rc = lbs_set_initial_device(h, nullptr, nullptr);
   if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(LBS_ECUDA, "initialisation failed");
   if (rc) {
@@ -560,6 +557,9 @@ int lbs_step(lbs_handle *h, int64_t n) {
 int lbs_sync(lbs_handle *h) {
   if (!h) return fail(LBS_EINVAL, "null handle");
   LBS_CK(cudaStreamSynchronize(h->stream));
+  int err = 0;
+  LBS_CK(cudaMemcpy(&err, h->errdev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) return fail(LBS_ETIMEOUT, "a kernel gave up waiting for its tile copies");
   return check_monitor(h, true);
 }
 
@@ -648,8 +648,16 @@ int lbs_set_graph_chunk(lbs_handle *h, int32_t k) {
 
 int lbs_set_variant(lbs_handle *h, int32_t variant) {
   if (!h || variant < 0 || variant >= h->L->nvariants) return fail(LBS_EINVAL, "unknown tile variant");
-  h->variant = variant;
-  return LBS_OK;
+  if (variant != h->variant) LBS_CK(cudaStreamSynchronize(h->stream));
+  return select_variant(h, variant);
+}
+
+int lbs_autotune_handle(lbs_handle *h, int32_t steps) {
+  if (!h) return fail(LBS_EINVAL, "null handle");
+  int32_t best = 0;
+  int rc = lbs_autotune(&h->lat, &h->mat, &h->bcs, steps, &best, nullptr);
+  if (rc) return rc;
+  return lbs_set_variant(h, best);
 }
 
 int64_t lbs_iteration(const lbs_handle *h) { return h ? h->k : -1; }

@@ -20,6 +20,8 @@
 // The collision at t therefore uses S(u(t)), as Sect. 3.1 requires.
 #pragma once
 #include <cuda_fp16.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -288,32 +290,40 @@ __device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t 
 // (1 - 1/(2 tau)) psi_q dt = w_q e.F, F = (1 - omega/2) sigma S.
 template <class R>
 __device__ __forceinline__ void collide(R f[9], R Sx, R Sy, R omega, R sigma) {
-  R r = 0, m1x = 0, m1y = 0, mxx = 0, mxy = 0, myy = 0;
-#pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    r += f[q];
-    if (ex(q)) m1x += R(ex(q)) * f[q];
-    if (ey(q)) m1y += R(ey(q)) * f[q];
-    if (ex(q)) mxx += f[q];
-    if (ex(q) * ey(q)) mxy += R(ex(q) * ey(q)) * f[q];
-    if (ey(q)) myy += f[q];
-  }
+  // opposite pairs (1,3), (2,4), (5,7), (6,8): even and odd parts
+  const R s13 = f[1] + f[3], s24 = f[2] + f[4], s57 = f[5] + f[7], s68 = f[6] + f[8];
+  const R d13 = f[1] - f[3], d24 = f[2] - f[4], d57 = f[5] - f[7], d68 = f[6] - f[8];
+  const R r = f[0] + (s13 + s24) + (s57 + s68);
+  const R m1x = d13 + (d57 - d68);
+  const R m1y = d24 + (d57 + d68);
+  const R Axx = R(3) * (s13 + (s57 + s68));
+  const R Ayy = R(3) * (s24 + (s57 + s68));
+  const R Axy = R(3) * (s57 - s68);
+  const R trA = Axx + Ayy;
   const R jx = R(3) * m1x + R(0.5) * sigma * Sx;
   const R jy = R(3) * m1y + R(0.5) * sigma * Sy;
-  const R Axx = R(3) * mxx, Axy = R(3) * mxy, Ayy = R(3) * myy;
-  const R half_trA = R(0.5) * (Axx + Ayy);
   const R fs = (R(1) - R(0.5) * omega) * sigma;
   const R Fx = fs * Sx, Fy = fs * Sy;
-#pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    const int e2 = ex(q) * ex(q) + ey(q) * ey(q);
-    const R rq = (e2 == 0) ? R(2) * r : ((e2 == 1) ? R(0.5) * r : -r);
-    const R eAe = R(ex(q) * ex(q)) * Axx + R(2 * ex(q) * ey(q)) * Axy + R(ey(q) * ey(q)) * Ayy;
-    const R ej = R(ex(q)) * jx + R(ey(q)) * jy;
-    const R eF = R(ex(q)) * Fx + R(ey(q)) * Fy;
-    const R feq = wq<R>(q) * (rq + ej + R(1.5) * eAe - half_trA);
-    f[q] = f[q] - omega * (f[q] - feq) + wq<R>(q) * eF;
-  }
+  const R w0 = wq<R>(0), w1 = wq<R>(1), w5 = wq<R>(5);
+  // even (E) and odd (J) parts of feq per pair, and the forcing term (Fq)
+  const R E0 = w0 * (R(2) * r - R(0.5) * trA);
+  const R Ex = w1 * (R(0.5) * r + R(1.5) * Axx - R(0.5) * trA);
+  const R Ey = w1 * (R(0.5) * r + R(1.5) * Ayy - R(0.5) * trA);
+  const R E57 = w5 * (trA - r + R(3) * Axy);
+  const R E68 = w5 * (trA - r - R(3) * Axy);
+  const R Jx = w1 * jx, Jy = w1 * jy, J57 = w5 * (jx + jy), J68 = w5 * (jy - jx);
+  const R Fqx = w1 * Fx, Fqy = w1 * Fy, F57 = w5 * (Fx + Fy), F68 = w5 * (Fy - Fx);
+  // g = f - omega (f - feq) + forcing: the non-equilibrium part f - feq is
+  // small, so this form keeps the rounding error relative to it
+  f[0] = f[0] - omega * (f[0] - E0);
+  f[1] = f[1] - omega * (f[1] - (Ex + Jx)) + Fqx;
+  f[3] = f[3] - omega * (f[3] - (Ex - Jx)) - Fqx;
+  f[2] = f[2] - omega * (f[2] - (Ey + Jy)) + Fqy;
+  f[4] = f[4] - omega * (f[4] - (Ey - Jy)) - Fqy;
+  f[5] = f[5] - omega * (f[5] - (E57 + J57)) + F57;
+  f[7] = f[7] - omega * (f[7] - (E57 - J57)) - F57;
+  f[6] = f[6] - omega * (f[6] - (E68 + J68)) + F68;
+  f[8] = f[8] - omega * (f[8] - (E68 - J68)) - F68;
 }
 
 // ------------------------------------------------------------------ tiles
@@ -643,6 +653,299 @@ cudaError_t launch_step(const Params &P, const StepPtrs &S, cudaStream_t st) {
   const int nedge = ntx * nty - ni * nj;
   if (nedge > 0) step_edge_kernel<C><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batches
+// A persistent-style walk over a tile table spanning many lattices of
+// different sizes: block i takes tiles i, i + grid, ...  Each tile runs the
+// same step_tile code as the single-lattice kernels, on its lattice's buffers
+// chosen by the parity of that lattice's iteration counter.
+template <class C, bool EDGE>
+__global__ void __launch_bounds__(C::NT) batch_step_kernel(const BatchLattice *lats, const BatchTile *tiles, int ntiles,
+                                                           int *err) {
+  __shared__ Params sP;
+  __shared__ StepPtrs sS;
+  __shared__ int skip;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const BatchTile T = tiles[t];
+      const BatchLattice &L = lats[T.lat];
+      skip = L.k >= L.kend;
+      if (!skip) {
+        sP = L.P;
+        const int p = (int)(L.k & 1);
+        sS.g_in = L.g[p];
+        sS.g_out = L.g[p ^ 1];
+        sS.u_in = L.u[p];
+        sS.u_out = L.u[p ^ 1];
+        sS.b_in = L.b[p];
+        sS.b_out = L.b[p ^ 1];
+        sS.kptr = &lats[T.lat].k;
+        sS.koff = 0;
+        sS.tm_g = sS.tm_u = nullptr;
+        sS.err = err;
+      }
+    }
+    __syncthreads();
+    if (!skip) {
+      const BatchTile T = tiles[t];
+      step_tile<C, EDGE>(sP, sS, T.a * C::TX, T.b * C::TY);
+    }
+    __syncthreads();  // the next tile reuses the shared memory
+  }
+}
+
+static __global__ void batch_advance_kernel(BatchLattice *lats, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && lats[i].k < lats[i].kend) lats[i].k += 1;
+}
+
+template <class C>
+cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
+                              int ne, int *err, cudaStream_t st) {
+  static int blocks = 0;
+  if (!blocks) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<C, false>, C::NT, 0);
+    blocks = sms * (per > 0 ? per : 1);
+  }
+  if (ni > 0) batch_step_kernel<C, false><<<ni < blocks ? ni : blocks, C::NT, 0, st>>>(lats, interior, ni, err);
+  if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, st>>>(lats, edge, ne, err);
+  if (nlats > 0) batch_advance_kernel<<<(nlats + 127) / 128, 128, 0, st>>>(lats, nlats);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ TMA-staged interior tiles
+// One 3-D TMA box brings the nine g planes of the tile plus a 3-node halo
+// (the streaming sources of the 2-node u halo) into shared memory, one 2-D
+// box brings u on the tile plus a 2-node halo; both complete on one mbarrier.
+// Streaming then reads shared memory, u(t+dt) is formed in place, and the
+// collision re-reads the streamed populations from shared memory.
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int c0, int c1, int c2, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_addr(dst)),
+      "l"((uint64_t)tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int c0, int c1, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"((uint64_t)tmap), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// bound on mbarrier polls (each try_wait also suspends in hardware for a while)
+constexpr uint32_t kMaxPolls = 1u << 22;
+
+template <class C>
+struct TmaCfg {
+  using gs = typename C::gs;
+  using us = typename C::us;
+  using real = typename C::real;
+  static constexpr int TX = C::TX, TY = C::TY;
+  static constexpr int ALIGN = 16 / (int)sizeof(gs);        // elements per 16 bytes
+  static constexpr int XO = ((3 + ALIGN - 1) / ALIGN) * ALIGN;  // smem column of node x0
+  static constexpr int GW = ((XO + TX + 3 + ALIGN - 1) / ALIGN) * ALIGN;  // box width
+  static constexpr int GH = TY + 6;                           // rows y0-3 .. y0+TY+2
+  static constexpr int UW = TX + 4, UH = TY + 4;              // u on R2
+  static constexpr int UEL = (int)(sizeof(us) / sizeof(real)); // reals per u record (2 or 4)
+  static constexpr size_t G_BYTES = (size_t)9 * GH * GW * sizeof(gs);
+  static constexpr size_t U_BYTES = (size_t)UH * UW * sizeof(us);
+  static constexpr size_t N_BYTES = (size_t)4 * (TY + 2) * (TX + 2) * sizeof(real);
+  static constexpr size_t OFF_U = (G_BYTES + 127) / 128 * 128;
+  static constexpr size_t OFF_N = OFF_U + (U_BYTES + 127) / 128 * 128;
+  static constexpr size_t OFF_BAR = OFF_N + (N_BYTES + 15) / 16 * 16;
+  static constexpr size_t SMEM = OFF_BAR + 16;
+};
+
+template <class C>
+__global__ void __launch_bounds__(C::NT) step_tma_kernel(const Params P, const StepPtrs S,
+                                                         const __grid_constant__ CUtensorMap tm_g,
+                                                         const __grid_constant__ CUtensorMap tm_u, int a_lo, int b_lo) {
+  using T = TmaCfg<C>;
+  using R = typename C::real;
+  using us = typename C::us;
+  using gs = typename C::gs;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  gs *sg = (gs *)dsm;                      // [9][GH][GW]
+  us *su = (us *)(dsm + T::OFF_U);         // [UH][UW]
+  R *snb = (R *)(dsm + T::OFF_N);          // [4][TY+2][TX+2]
+  uint64_t *bar = (uint64_t *)(dsm + T::OFF_BAR);
+  const int x0 = (a_lo + blockIdx.x) * C::TX, y0 = (b_lo + blockIdx.y) * C::TY;
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, (uint32_t)(T::G_BYTES + T::U_BYTES));
+    tma_load_3d(sg, &tm_g, x0 - T::XO, y0 - 3, 0, bar);
+    tma_load_2d(su, &tm_u, T::UEL * (x0 - 2), y0 - 2, bar);
+  }
+  __syncthreads();  // the barrier is initialised before anyone polls it
+  int ok = 0;
+  for (uint32_t i = 0; i < kMaxPolls; ++i)
+    if (mbar_try_wait(bar, 0)) {
+      ok = 1;
+      break;
+    }
+  if (!__syncthreads_and(ok)) {
+    // the copies did not land in time: report and leave without touching
+    // the tile (the host turns the flag into LBS_ETIMEOUT)
+    if (threadIdx.x == 0 && S.err) atomicExch(S.err, 1);
+    return;
+  }
+
+  const R inv = (R)ldexp(1.0, -P.gshift), scl = (R)ldexp(1.0, P.gshift);
+  const R kap = (R)P.kappa;
+  auto G = [&](int q, int r, int c) -> R {
+    const gs v = sg[((size_t)q * T::GH + r) * T::GW + c];
+    if constexpr (sizeof(gs) == 2) return __half2float(v) * inv;
+    else return (R)v;
+  };
+  // phase 1: u(t+dt) on R2, in place (R2 position (cx, cy) = node (x0-2+cx, y0-2+cy);
+  // its g row is cy+1, its g column cx+XO-2)
+  for (int e = threadIdx.x; e < T::UW * T::UH; e += C::NT) {
+    const int cx = e % T::UW, cy = e / T::UW;
+    const int gr = cy + 1, gc = cx + T::XO - 2;
+    R p[9], o[9];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) {
+      p[q] = G(q, gr - ey(q), gc - ex(q));
+      o[q] = G(q, gr, gc);
+    }
+    // same grouping as gather(): first moments of own and streamed populations
+    const R gx = (o[1] - o[3]) + (o[5] - o[6]) + (o[8] - o[7]);
+    const R gy = (o[2] - o[4]) + (o[5] - o[8]) + (o[6] - o[7]);
+    const R fx = (p[1] - p[3]) + (p[5] - p[6]) + (p[8] - p[7]);
+    const R fy = (p[2] - p[4]) + (p[5] - p[8]) + (p[6] - p[7]);
+    su[e] = uadd(su[e], kap * (gx + fx), kap * (gy + fy));
+  }
+  __syncthreads();
+  // phase 2: N on R1
+  {
+    const R lam = (R)P.lam, mu = (R)P.mu, hdx = R(0.5) * (R)P.inv_dx;
+    constexpr int W1 = C::TX + 2, H1 = C::TY + 2;
+    for (int e = threadIdx.x; e < W1 * H1; e += C::NT) {
+      const int rx = e % W1, ry = e / W1;
+      const int c = (ry + 1) * T::UW + (rx + 1);
+      R dxx, dxy, dyx, dyy, H[4], N[4];
+      udiff(su[c + 1], su[c - 1], dxx, dxy);
+      udiff(su[c + T::UW], su[c - T::UW], dyx, dyy);
+      H[0] = dxx * hdx;
+      H[1] = dyx * hdx;
+      H[2] = dxy * hdx;
+      H[3] = dyy * hdx;
+      material<R>(P, lam, mu, H, N);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) snb[(m * H1 + ry) * W1 + rx] = N[m];
+    }
+  }
+  __syncthreads();
+  // phase 3: stream again from shared memory, source, collision, store
+  const size_t plane = (size_t)P.ny * P.pitch;
+  const R omega = (R)P.omega, sigma = (R)P.sigma, hdx = R(0.5) * (R)P.inv_dx;
+  const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
+  gs *__restrict__ go = (gs *)S.g_out;
+  us *__restrict__ uo = (us *)S.u_out;
+  constexpr int W1 = C::TX + 2, H1 = C::TY + 2;
+  const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
+#pragma unroll
+  for (int i = 0; i < C::CPT; ++i) {
+    const int lx = tx, ly = ty + i * C::NTY;
+    const int gr = ly + 3, gc = lx + T::XO;
+    R f[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = G(q, gr - ey(q), gc - ex(q));
+    const int rx = lx + 1, ry = ly + 1;
+    auto n = [&](int m, int yy, int xx) -> R { return snb[(m * H1 + yy) * W1 + xx]; };
+    const R Sx = (n(0, ry, rx + 1) - n(0, ry, rx - 1)) * hdx + (n(1, ry + 1, rx) - n(1, ry - 1, rx)) * hdx + sbx;
+    const R Sy = (n(2, ry, rx + 1) - n(2, ry, rx - 1)) * hdx + (n(3, ry + 1, rx) - n(3, ry - 1, rx)) * hdx + sby;
+    collide<R>(f, Sx, Sy, omega, sigma);
+    const size_t idx = (size_t)(y0 + ly) * P.pitch + (x0 + lx);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[q], scl);
+    uo[idx] = su[(ly + 2) * T::UW + (lx + 2)];
+  }
+}
+
+template <class C>
+cudaError_t launch_step_tma(const Params &P, const StepPtrs &S, cudaStream_t st) {
+  using T = TmaCfg<C>;
+  const int ntx = (P.nx + C::TX - 1) / C::TX, nty = (P.ny + C::TY - 1) / C::TY;
+  int a_lo, a_hi, b_lo, b_hi;
+  interior_range(P.nx, P.ny, C::TX, C::TY, a_lo, a_hi, b_lo, b_hi);
+  const int ni = a_hi - a_lo, nj = b_hi - b_lo;
+  if (ni > 0 && nj > 0) {
+    if (!S.tm_g || !S.tm_u) return cudaErrorInvalidValue;
+    step_tma_kernel<C><<<dim3(ni, nj), C::NT, T::SMEM, st>>>(P, S, *(const CUtensorMap *)S.tm_g,
+                                                               *(const CUtensorMap *)S.tm_u, a_lo, b_lo);
+  }
+  const int nedge = ntx * nty - ni * nj;
+  if (nedge > 0) step_edge_kernel<C><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+  return cudaGetLastError();
+}
+
+// TMA descriptors for one (g, u) buffer pair and the kernel's shared-memory
+// opt-in (host side; called when a handle selects a TMA tile variant)
+template <class C>
+bool make_tma_maps(const Params &P, const void *g, const void *u, void *out_g, void *out_u) {
+  using T = TmaCfg<C>;
+  using gs = typename C::gs;
+  using R = typename C::real;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const CUtensorMapDataType gt = sizeof(gs) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : sizeof(gs) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const cuuint64_t gdim[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.ny, 9};
+  const cuuint64_t gstr[2] = {(cuuint64_t)P.pitch * sizeof(gs), (cuuint64_t)P.ny * P.pitch * sizeof(gs)};
+  const cuuint32_t gbox[3] = {(cuuint32_t)T::GW, (cuuint32_t)T::GH, 9};
+  const cuuint32_t est[3] = {1, 1, 1};
+  CUresult r1 = encode((CUtensorMap *)out_g, gt, 3, const_cast<void *>(g), gdim, gstr, gbox, est,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUtensorMapDataType ut = sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t udim[2] = {(cuuint64_t)T::UEL * P.pitch, (cuuint64_t)P.ny};
+  const cuuint64_t ustr[1] = {(cuuint64_t)T::UEL * P.pitch * sizeof(R)};
+  const cuuint32_t ubox[2] = {(cuuint32_t)(T::UEL * T::UW), (cuuint32_t)T::UH};
+  CUresult r2 = encode((CUtensorMap *)out_u, ut, 2, const_cast<void *>(u), udim, ustr, ubox, est,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return false;
+  return cudaFuncSetAttribute(step_tma_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM) ==
+         cudaSuccess;
 }
 
 // ------------------------------------------------------------------ init / fields

@@ -1,5 +1,6 @@
 // Host-side declarations shared by the liblbs translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,19 +45,41 @@ struct StepPtrs {
   void *b_out;
   const int64_t *kptr;  // iteration counter base (device)
   int64_t koff;         // iteration = *kptr + koff
+  const void *tm_g;     // host pointers to the TMA descriptors of g_in and
+  const void *tm_u;     //   u_in (TMA tile variants only)
+  int *err;             // device flag set when a bounded wait gives up
 };
 
 struct TileShape {
   int tx, ty;
 };
 
+// One resident lattice of a batch (device memory): its parameters, both
+// buffers of each state array, and its iteration counter and end.
+struct BatchLattice {
+  Params P;
+  void *g[2], *u[2], *b[2];
+  int64_t k;     // iteration of the state in buffers [k & 1]; advanced on the device
+  int64_t kend;  // the lattice stops here (its tiles return at once)
+};
+
+// One tile of a batch: lattice index and tile coordinates (in tiles).
+struct BatchTile {
+  int lat, a, b;
+};
+
 // Launchers, one set per precision (kernels_fp*.cu).  `variant` picks a tile
 // shape (0 = default).  Return a cudaError_t of the launch.
 struct Launchers {
   int nvariants;
+  int tma_index;  // the variant whose interior tiles are staged by TMA
+  int default_variant;
   TileShape (*shape)(int variant);
   cudaError_t (*step)(const Params &p, const StepPtrs &s, int variant, cudaStream_t st);
   int (*kernels_per_step)(const Params &p, int variant);
+  // TMA descriptors of one (g, u) buffer pair for a tile variant; returns
+  // false if the variant does not use TMA.  out_g/out_u: CUtensorMap storage.
+  bool (*tma_maps)(const Params &p, int variant, const void *g, const void *u, void *out_g, void *out_u);
   cudaError_t (*init)(const Params &p, void *g, void *u, void *b, const double *u0, const double *v0,
                       cudaStream_t st);
   cudaError_t (*fields)(const Params &p, const void *g, const void *u, double *uo, double *vo, double *Po,
@@ -64,6 +87,12 @@ struct Launchers {
   cudaError_t (*monitor)(const Params &p, const void *g, const void *u, double *partials, int nblocks,
                          double *out6, cudaStream_t st);
   cudaError_t (*probe)(const Params &p, const void *u, const int32_t *idx, int n, double *out, cudaStream_t st);
+  // one iteration of every unfinished lattice of a batch: interior tiles,
+  // frame tiles, then the per-lattice counters (tile shape of the default
+  // global-memory variant, batch_tile())
+  cudaError_t (*batch_step)(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
+                            int ne, int *err, cudaStream_t st);
+  TileShape batch_tile;
   size_t g_elem, u_elem, b_elem;  // bytes per stored g value, per u record, per boundary entry
 };
 
@@ -76,4 +105,50 @@ int monitor_blocks(const Params &p);
 
 void set_error(const std::string &msg);
 
+// device allocator of a handle (lbs_set_allocator or cudaMalloc)
+struct Allocator {
+  lbs_alloc_fn alloc;
+  lbs_free_fn release;
+  void *ctx;
+};
+
 }  // namespace lbs
+
+// State of one lattice (the C ABI's opaque lbs_handle).
+struct lbs_handle {
+  lbs::Params P;
+  int precision;
+  const lbs::Launchers *L;
+  int variant;
+  lbs::Allocator alloc;
+  cudaStream_t own_stream;
+  cudaStream_t stream;
+  void *g[2], *u[2], *b[2];
+  void *mon_block;          // partials, out[8], counters
+  double *mon_partials;
+  double *mon_out;          // device: bad, max|u|, mx, my, mass, flag
+  int64_t *kdev;            // device iteration base used by graph replays
+  int64_t *zero_dev;        // device constant 0 (direct launches)
+  double *mon_host;         // pinned copy of mon_out
+  cudaEvent_t mon_event;
+  bool mon_pending;
+  int64_t mon_k;            // iteration of the pending monitor
+  int64_t mon_interval, next_mon;
+  int parity;               // the current state sits in buffers [parity]
+  int64_t k;                // iteration counter
+  int64_t kdev_value;       // value held by *kdev (host mirror)
+  int64_t unstable_at;
+  int graph_chunk;
+  cudaGraphExec_t graph[2];
+  int graph_variant[2];
+  size_t bytes;
+  int cfl_warn;
+  int64_t launches;         // kernels launched for this handle
+  int *errdev;              // device flag: a bounded wait in a kernel gave up
+  CUtensorMap tm_g[2];      // TMA descriptors of g[0], g[1] and u[0], u[1]
+  CUtensorMap tm_u[2];      //   for the current variant (TMA variants only)
+  bool tma;                 // the current variant stages tiles with TMA
+  lbs_lattice lat;          // the configuration the handle was created with
+  lbs_material mat;
+  lbs_bcs bcs;
+};

@@ -1,0 +1,403 @@
+// Continuous-batching server of liblbs (include/lbs_serve.h): admission by
+// device footprint, resident state, one batched step kernel per iteration over
+// a tile table spanning all resident lattices, retirement at chunk boundaries.
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lbs_serve.h"
+#include "lbs_device.cuh"
+#include "lbs_internal.h"
+
+using lbs::BatchLattice;
+using lbs::BatchTile;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+  uint64_t id = 0;
+  lbs_lattice lat;
+  lbs_material mat;
+  lbs_bcs bcs;
+  int64_t nsteps = 0;
+  int state = LBS_TICKET_QUEUED;
+  int error = LBS_OK;
+  int64_t k = 0;
+  double t_submit = 0, t_admit = -1, t_done = -1;
+  size_t bytes = 0;
+  lbs_handle *h = nullptr;
+  std::vector<double> u, v, P;
+};
+
+}  // namespace
+
+struct lbs_server {
+  lbs_server_config cfg;
+  int device = 0;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  std::deque<Req *> queue;
+  std::map<uint64_t, Req *> tickets;
+  uint64_t next_id = 1;
+  size_t used = 0;
+  Clock::time_point t0;
+  lbs_server_stats st;
+  // owned by the worker thread
+  cudaStream_t stream = nullptr;
+  BatchLattice *d_lats = nullptr;
+  int lat_cap = 0;
+  BatchTile *d_tiles = nullptr;
+  int tile_cap = 0;
+  int *d_err = nullptr;
+
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+void finish(lbs_server *s, Req *r, int error) {
+  // the batch advanced the state outside the handle: bring it up to date
+  lbs_handle *h = r->h;
+  if (h) {
+    h->k = r->k;
+    h->parity = (int)(r->k & 1);
+    h->kdev_value = -1;
+    if (!error) {
+      lbs_monitors m;
+      if (lbs_monitor(h, &m) == LBS_OK && m.nonfinite > 0) error = LBS_EUNSTABLE;
+    }
+    const size_t n = (size_t)r->lat.nx * r->lat.ny;
+    r->u.resize(2 * n);
+    r->v.resize(2 * n);
+    r->P.resize(4 * n);
+    if (lbs_fields(h, r->u.data(), r->v.data(), r->P.data()) != LBS_OK && !error) error = LBS_ECUDA;
+    lbs_destroy(h);
+    r->h = nullptr;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->used -= r->bytes;
+  r->error = error;
+  r->state = error ? LBS_TICKET_FAILED : LBS_TICKET_DONE;
+  r->t_done = s->now();
+  s->st.resident -= 1;
+  if (error) s->st.failed += 1;
+  else s->st.completed += 1;
+  s->st.node_updates += (int64_t)r->lat.nx * r->lat.ny * r->k;
+  s->cv_done.notify_all();
+}
+
+template <class T>
+bool ensure(T *&ptr, int &cap, int need) {
+  if (need <= cap) return true;
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  int c = std::max(need, 2 * cap);
+  if (cudaMalloc(&ptr, sizeof(T) * (size_t)c) != cudaSuccess) {
+    cudaGetLastError();
+    cap = 0;
+    return false;
+  }
+  cap = c;
+  return true;
+}
+
+void run(lbs_server *s) {
+  cudaSetDevice(s->device);
+  std::vector<Req *> res;
+  std::vector<BatchLattice> hl;
+  std::vector<BatchTile> ht;
+  int ni = 0, ne = 0;
+  bool dirty = true;
+  const lbs::Launchers &L = s->cfg.precision == LBS_FP64   ? lbs::launchers_fp64()
+                            : s->cfg.precision == LBS_FP32 ? lbs::launchers_fp32()
+                                                           : lbs::launchers_fp16();
+  for (;;) {
+    // admission: FIFO while the footprint fits
+    std::vector<Req *> admit;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (res.empty() && s->queue.empty()) {
+        if (s->stop) break;
+        s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+        if (s->stop && s->queue.empty()) break;
+      }
+      if (s->stop) break;
+      while (!s->queue.empty()) {
+        Req *r = s->queue.front();
+        if (s->cfg.max_resident > 0 && (int)(res.size() + admit.size()) >= s->cfg.max_resident) break;
+        if (s->used + r->bytes > s->cfg.hbm_budget) break;
+        s->queue.pop_front();
+        s->used += r->bytes;
+        s->st.queued -= 1;
+        s->st.resident += 1;
+        admit.push_back(r);
+      }
+    }
+    for (Req *r : admit) {
+      const int rc = lbs_create(&r->lat, &r->mat, &r->bcs, &r->h);
+      if (rc) {
+        r->h = nullptr;
+        finish(s, r, rc);
+        continue;
+      }
+      lbs_set_monitor_interval(r->h, 0);
+      std::lock_guard<std::mutex> lk(s->mu);
+      r->state = LBS_TICKET_RUNNING;
+      r->t_admit = s->now();
+      res.push_back(r);
+      dirty = true;
+    }
+    if (res.empty()) continue;
+    // batch tables
+    if (dirty) {
+      hl.resize(res.size());
+      ht.clear();
+      std::vector<BatchTile> edge;
+      const int TX = L.batch_tile.tx, TY = L.batch_tile.ty;
+      for (size_t i = 0; i < res.size(); ++i) {
+        lbs_handle *h = res[i]->h;
+        BatchLattice &B = hl[i];
+        B.P = h->P;
+        for (int p = 0; p < 2; ++p) {
+          B.g[p] = h->g[p];
+          B.u[p] = h->u[p];
+          B.b[p] = h->b[p];
+        }
+        B.k = res[i]->k;
+        B.kend = res[i]->nsteps;
+        const int ntx = (h->P.nx + TX - 1) / TX, nty = (h->P.ny + TY - 1) / TY;
+        int a_lo, a_hi, b_lo, b_hi;
+        lbs::interior_range(h->P.nx, h->P.ny, TX, TY, a_lo, a_hi, b_lo, b_hi);
+        for (int b = 0; b < nty; ++b)
+          for (int a = 0; a < ntx; ++a) {
+            const bool in = a >= a_lo && a < a_hi && b >= b_lo && b < b_hi;
+            (in ? ht : edge).push_back(BatchTile{(int)i, a, b});
+          }
+      }
+      ni = (int)ht.size();
+      ne = (int)edge.size();
+      ht.insert(ht.end(), edge.begin(), edge.end());
+      if (!ensure(s->d_lats, s->lat_cap, (int)hl.size()) || !ensure(s->d_tiles, s->tile_cap, (int)ht.size())) {
+        for (Req *r : res) finish(s, r, LBS_ENOMEM);
+        res.clear();
+        continue;
+      }
+      cudaMemcpyAsync(s->d_lats, hl.data(), sizeof(BatchLattice) * hl.size(), cudaMemcpyHostToDevice, s->stream);
+      cudaMemcpyAsync(s->d_tiles, ht.data(), sizeof(BatchTile) * ht.size(), cudaMemcpyHostToDevice, s->stream);
+      dirty = false;
+    }
+    // one chunk of iterations for every resident lattice
+    int64_t chunk = s->cfg.chunk;
+    int64_t longest = 0;
+    for (Req *r : res) longest = std::max(longest, r->nsteps - r->k);
+    chunk = std::min(chunk, longest);
+    const double tb = s->now();
+    int64_t launched = 0;
+    for (int64_t it = 0; it < chunk; ++it) {
+      L.batch_step(s->d_lats, (int)res.size(), s->d_tiles, ni, s->d_tiles + ni, ne, s->d_err, s->stream);
+      launched += (ni > 0) + (ne > 0) + 1;
+    }
+    const cudaError_t e = cudaStreamSynchronize(s->stream);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->st.busy_seconds += s->now() - tb;
+      s->st.launches += launched;
+      for (Req *r : res) r->k = std::min(r->k + chunk, r->nsteps);
+    }
+    // retire finished lattices
+    std::vector<Req *> keep;
+    for (Req *r : res) {
+      if (e != cudaSuccess) finish(s, r, LBS_ECUDA);
+      else if (r->k >= r->nsteps) finish(s, r, LBS_OK);
+      else keep.push_back(r);
+    }
+    if (keep.size() != res.size()) dirty = true;
+    res.swap(keep);
+  }
+  // shutdown: release what is still resident
+  for (Req *r : res) {
+    if (r->h) lbs_destroy(r->h);
+    r->h = nullptr;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbs_server_create(const lbs_server_config *cfg, lbs_server **out) {
+  if (!cfg || !out || cfg->precision < LBS_FP64 || cfg->precision > LBS_FP16S || cfg->chunk < 0 ||
+      cfg->max_resident < 0 || cfg->queue_limit < 0) {
+    lbs::set_error("bad server configuration");
+    return LBS_EINVAL;
+  }
+  lbs_server *s = new lbs_server();
+  s->cfg = *cfg;
+  if (s->cfg.chunk == 0) s->cfg.chunk = 64;
+  memset(&s->st, 0, sizeof(s->st));
+  s->t0 = Clock::now();
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&s->d_err, sizeof(int)) != cudaSuccess || cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    lbs::set_error("server: CUDA set-up failed");
+    return LBS_ECUDA;
+  }
+  if (s->cfg.hbm_budget == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    s->cfg.hbm_budget = fr / 10 * 8;
+  }
+  s->st.hbm_budget = s->cfg.hbm_budget;
+  s->worker = std::thread(run, s);
+  *out = s;
+  return LBS_OK;
+}
+
+int lbs_submit(lbs_server *s, const lbs_lattice *lat, const lbs_material *mat, const lbs_bcs *bcs, int64_t nsteps,
+               uint64_t *ticket) {
+  if (!s || !lat || !mat || !ticket || nsteps < 0) return LBS_EINVAL;
+  Req *r = new Req();
+  r->lat = *lat;
+  r->lat.precision = s->cfg.precision;
+  r->mat = *mat;
+  if (bcs) {
+    r->bcs = *bcs;
+  } else {
+    memset(&r->bcs, 0, sizeof(r->bcs));
+    for (int e = 0; e < 4; ++e) r->bcs.edge[e].type = LBS_NEUMANN;
+  }
+  double p[5];
+  int rc = lbs_params(&r->lat, &r->mat, p);
+  if (rc) {
+    delete r;
+    return rc;
+  }
+  r->nsteps = nsteps;
+  r->bytes = lbs_footprint(&r->lat);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (r->bytes > s->cfg.hbm_budget) {
+    delete r;
+    lbs::set_error("request larger than the server's HBM budget");
+    return LBS_ENOMEM;
+  }
+  if (s->cfg.queue_limit > 0 && (int64_t)s->queue.size() >= s->cfg.queue_limit) {
+    delete r;
+    lbs::set_error("queue full");
+    return LBS_EBUSY;
+  }
+  r->id = s->next_id++;
+  r->t_submit = s->now();
+  s->tickets[r->id] = r;
+  s->queue.push_back(r);
+  s->st.submitted += 1;
+  s->st.queued += 1;
+  *ticket = r->id;
+  s->cv_work.notify_one();
+  return LBS_OK;
+}
+
+int lbs_poll(lbs_server *s, uint64_t ticket, lbs_ticket_info *info) {
+  if (!s || !info) return LBS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->tickets.find(ticket);
+  if (it == s->tickets.end()) return LBS_ENOTFOUND;
+  const Req *r = it->second;
+  info->state = r->state;
+  info->error = r->error;
+  info->iterations = r->k;
+  info->nsteps = r->nsteps;
+  info->nx = r->lat.nx;
+  info->ny = r->lat.ny;
+  info->t_submit = r->t_submit;
+  info->t_admit = r->t_admit;
+  info->t_done = r->t_done;
+  info->device_bytes = r->bytes;
+  return LBS_OK;
+}
+
+int lbs_wait(lbs_server *s, uint64_t ticket, double timeout_s) {
+  if (!s) return LBS_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto done = [&] {
+    auto it = s->tickets.find(ticket);
+    return it == s->tickets.end() || it->second->state >= LBS_TICKET_DONE;
+  };
+  if (s->tickets.find(ticket) == s->tickets.end()) return LBS_ENOTFOUND;
+  if (timeout_s < 0) s->cv_done.wait(lk, done);
+  else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done)) return LBS_ETIMEOUT;
+  return LBS_OK;
+}
+
+int lbs_result(lbs_server *s, uint64_t ticket, double *u, double *v, double *P) {
+  if (!s) return LBS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->tickets.find(ticket);
+  if (it == s->tickets.end()) return LBS_ENOTFOUND;
+  Req *r = it->second;
+  if (r->state < LBS_TICKET_DONE) return LBS_EBUSY;
+  if (u && !r->u.empty()) memcpy(u, r->u.data(), r->u.size() * sizeof(double));
+  if (v && !r->v.empty()) memcpy(v, r->v.data(), r->v.size() * sizeof(double));
+  if (P && !r->P.empty()) memcpy(P, r->P.data(), r->P.size() * sizeof(double));
+  const int err = r->error;
+  s->tickets.erase(it);
+  delete r;
+  return err;
+}
+
+int lbs_server_drain(lbs_server *s, double timeout_s) {
+  if (!s) return LBS_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto idle = [&] {
+    for (auto &kv : s->tickets)
+      if (kv.second->state < LBS_TICKET_DONE) return false;
+    return true;
+  };
+  if (timeout_s < 0) s->cv_done.wait(lk, idle);
+  else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), idle)) return LBS_ETIMEOUT;
+  return LBS_OK;
+}
+
+int lbs_server_get_stats(lbs_server *s, lbs_server_stats *out) {
+  if (!s || !out) return LBS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->st;
+  out->bytes_in_use = s->used;
+  return LBS_OK;
+}
+
+int lbs_server_destroy(lbs_server *s) {
+  if (!s) return LBS_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto &kv : s->tickets) {
+    if (kv.second->h) lbs_destroy(kv.second->h);
+    delete kv.second;
+  }
+  if (s->d_lats) cudaFree(s->d_lats);
+  if (s->d_tiles) cudaFree(s->d_tiles);
+  if (s->d_err) cudaFree(s->d_err);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+  return LBS_OK;
+}
+
+}  // extern "C"

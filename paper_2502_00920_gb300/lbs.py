@@ -91,9 +91,48 @@ SIGNATURES = {
     "lbs_footprint": (ctypes.c_size_t, [ctypes.POINTER(Lattice)]),
     "lbs_constitutive": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]),
     "lbs_tile_variants": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, _i32p]),
+    "lbs_tile_variant_kind": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     "lbs_set_allocator": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lbs_autotune": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(Material), ctypes.POINTER(Bcs),
+                                    ctypes.c_int32, _i32p, ctypes.POINTER(ctypes.c_float)]),
+    "lbs_autotune_handle": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "lbs_autotune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "lbs_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "lbs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lbs_last_error": (ctypes.c_char_p, []),
+}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("precision", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("max_resident", ctypes.c_int32), ("queue_limit", ctypes.c_int32)]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("error", ctypes.c_int32), ("iterations", ctypes.c_int64),
+                ("nsteps", ctypes.c_int64), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("node_updates", ctypes.c_int64),
+                ("busy_seconds", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t),
+                ("launches", ctypes.c_int64)]
+
+
+# include/lbs_serve.h
+SERVE_SIGNATURES = {
+    "lbs_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
+    "lbs_submit": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(Material), ctypes.POINTER(Bcs),
+                                  ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]),
+    "lbs_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(TicketInfo)]),
+    "lbs_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double]),
+    "lbs_result": (ctypes.c_int, [_vp, ctypes.c_uint64, _dp, _dp, _dp]),
+    "lbs_server_drain": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "lbs_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
+    "lbs_server_destroy": (ctypes.c_int, [_vp]),
 }
 
 
@@ -105,7 +144,7 @@ def lib():
             if not os.path.exists(LIB_PATH):
                 raise LbsError(ECUDA, f"{LIB_PATH} is missing; build it with __graft_entry__.build()")
             L = ctypes.CDLL(LIB_PATH)
-            for name, (res, args) in SIGNATURES.items():
+            for name, (res, args) in {**SIGNATURES, **SERVE_SIGNATURES}.items():
                 fn = getattr(L, name)
                 fn.restype = res
                 fn.argtypes = args
@@ -166,6 +205,30 @@ def tile_variants(precision: str = "fp32"):
     return [(tx[i], ty[i]) for i in range(n.value)]
 
 
+def autotune(case, steps: int = 20):
+    """(best variant, per-variant ms per iteration) for a Case (cached per configuration)."""
+    lat, mat, bcs = structs(case)
+    best = ctypes.c_int32()
+    ms = (ctypes.c_float * 16)()
+    check(lib().lbs_autotune(ctypes.byref(lat), ctypes.byref(mat), ctypes.byref(bcs), int(steps), ctypes.byref(best), ms))
+    return best.value, [ms[i] for i in range(len(tile_variants(case.precision)))]
+
+
+def autotune_save(path: str):
+    check(lib().lbs_autotune_save(str(path).encode()))
+
+
+def autotune_load(path: str):
+    check(lib().lbs_autotune_load(str(path).encode()))
+
+
+def tile_variant_kind(precision: str, variant: int) -> str:
+    k = lib().lbs_tile_variant_kind(PRECISION[precision], int(variant))
+    if k < 0:
+        check(k)
+    return "tma" if k == 1 else "global"
+
+
 def _dev_ptr(t):
     if t is None:
         return None
@@ -192,7 +255,9 @@ class Simulation:
             check(lib().lbs_set_graph_chunk(self._h, int(graph_chunk)))
         if monitor_interval is not None:
             check(lib().lbs_set_monitor_interval(self._h, int(monitor_interval)))
-        if variant is not None:
+        if variant == "auto":
+            check(lib().lbs_autotune_handle(self._h, 20))
+        elif variant is not None:
             check(lib().lbs_set_variant(self._h, int(variant)))
         if u0 is not None or v0 is not None:
             self.set_initial(u0, v0)
@@ -303,3 +368,73 @@ class Simulation:
     @property
     def launch_count(self) -> int:
         return int(lib().lbs_launch_count(self._h))
+
+
+TICKET_STATES = ("queued", "running", "done", "failed")
+
+
+class Server:
+    """Continuous-batching server (include/lbs_serve.h)."""
+
+    def __init__(self, precision: str = "fp32", hbm_budget: int = 0, chunk: int = 64, max_resident: int = 0,
+                 queue_limit: int = 0):
+        cfg = ServerConfig(int(hbm_budget), PRECISION[precision], int(chunk), int(max_resident), int(queue_limit))
+        h = _vp()
+        check(lib().lbs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.precision = precision
+        self._cases = {}
+
+    def submit(self, case) -> int:
+        lat, mat, bcs = structs(case)
+        t = ctypes.c_uint64()
+        check(lib().lbs_submit(self._h, ctypes.byref(lat), ctypes.byref(mat), ctypes.byref(bcs), int(case.nsteps),
+                               ctypes.byref(t)))
+        self._cases[t.value] = case
+        return t.value
+
+    def poll(self, ticket: int) -> dict:
+        info = TicketInfo()
+        check(lib().lbs_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(info)))
+        return dict(state=TICKET_STATES[info.state], error=info.error, iterations=info.iterations,
+                    nsteps=info.nsteps, nx=info.nx, ny=info.ny, t_submit=info.t_submit, t_admit=info.t_admit,
+                    t_done=info.t_done, device_bytes=info.device_bytes)
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        check(lib().lbs_wait(self._h, ctypes.c_uint64(ticket), float(timeout)))
+
+    def result(self, ticket: int):
+        """(u, v, P, error code) of a finished ticket; forgets the ticket."""
+        case = self._cases.pop(ticket)
+        ny, nx = case.ny, case.nx
+        u, v, P = np.empty((ny, nx, 2)), np.empty((ny, nx, 2)), np.empty((ny, nx, 4))
+        rc = lib().lbs_result(self._h, ctypes.c_uint64(ticket), _ptr(u), _ptr(v), _ptr(P))
+        if rc not in (OK, EUNSTABLE):
+            self._cases[ticket] = case
+            check(rc)
+        return u, v, P, rc
+
+    def drain(self, timeout: float = -1.0):
+        check(lib().lbs_server_drain(self._h, float(timeout)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(lib().lbs_server_get_stats(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbs_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,134 @@
+"""Continuous-batching server on the GPU: each result equals the same lattice
+run alone (and the oracle within the precision's bar), admission respects
+the HBM budget, requests arriving while others run are admitted as memory
+frees up, and failures are reported per ticket."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2502_00920_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2502_00920_gb300 import build
+    build.build()
+    from paper_2502_00920_gb300 import lbs
+    return lbs
+
+
+def mix(precision="fp32"):
+    trac = I.Edge("neumann", "linear_ramp", (0.01, 0.0), 0, 80)
+    return [
+        I.tension(32, 32, 150, ramp=100, model="nh", precision=precision),
+        I.shear(64, 220, model="svk", nu=0.2, gamma=0.05, ramp=400, precision=precision),
+        I.cantilever(200, 24, 90, width=60, amp=0.01, nu=0.25, precision=precision),
+        I.Case("m", 130, 70, 300, model="svk", nu=0.2, edges=(I.CLAMPED, trac, I.FREE, I.FREE), precision=precision),
+        I.Case("p", 96, 40, 64, model="nh", nu=0.1, edges=(I.FREE, trac, I.CLAMPED, I.FREE), precision=precision),
+        I.tension(45, 33, 77, ramp=40, model="svk", nu=0.0, precision=precision),
+    ]
+
+
+def alone(L, case):
+    with L.Simulation(case) as s:
+        s.step(case.nsteps)
+        s.sync()
+        return s.fields()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_mixed_batch_equals_alone(L, precision):
+    cases = mix(precision)
+    with L.Server(precision=precision, chunk=32) as srv:
+        tickets = [srv.submit(c) for c in cases]
+        srv.drain(120)
+        results = [srv.result(t) for t in tickets]
+    for c, (u, v, P, rc) in zip(cases, results):
+        assert rc == L.OK
+        ua, va, Pa = alone(L, c)
+        assert np.array_equal(u, ua) and np.array_equal(v, va) and np.array_equal(P, Pa), c.name
+
+
+def test_batch_matches_oracle(L, oracle_mod):
+    cases = mix("fp64")[:3]
+    with L.Server(precision="fp64", chunk=16) as srv:
+        tickets = [srv.submit(c) for c in cases]
+        srv.drain(120)
+        results = [srv.result(t) for t in tickets]
+    for c, (u, v, P, rc) in zip(cases, results):
+        o = oracle_mod.OracleSim(c)
+        o.step(c.nsteps)
+        ur = o.fields()[0]
+        assert np.abs(u - ur).max() <= 1e-12 * np.abs(ur).max()
+
+
+def test_admission_respects_budget(L):
+    case = I.tension(256, 128, 400, ramp=100, model="nh")
+    fp = L.footprint(case.replace(precision="fp32"))
+    budget = int(2.5 * fp)
+    peak = 0
+    with L.Server(precision="fp32", hbm_budget=budget, chunk=16) as srv:
+        tickets = [srv.submit(case) for _ in range(5)]
+        while srv.stats()["completed"] + srv.stats()["failed"] < 5:
+            st = srv.stats()
+            peak = max(peak, st["bytes_in_use"])
+            assert st["resident"] <= 2
+            time.sleep(0.002)
+        infos = [srv.poll(t) for t in tickets]
+        for t in tickets:
+            srv.result(t)
+    assert 0 < peak <= budget
+    assert all(i["state"] == "done" for i in infos)
+    # at most two at a time: the third is admitted only after one finished
+    admits = sorted(i["t_admit"] for i in infos)
+    dones = sorted(i["t_done"] for i in infos)
+    assert admits[2] >= dones[0] - 1e-6
+
+
+def test_continuous_admission(L):
+    """Requests arriving while others are on the GPU join the running batch."""
+    long = I.tension(512, 256, 3000, ramp=500, model="nh")
+    short = [I.tension(64, 48, 200, ramp=50, model="svk", nu=0.1) for _ in range(4)]
+    with L.Server(precision="fp32", chunk=32) as srv:
+        t_long = srv.submit(long)
+        time.sleep(0.05)
+        ts = []
+        for c in short:
+            ts.append(srv.submit(c))
+            time.sleep(0.01)
+        srv.drain(120)
+        il = srv.poll(t_long)
+        infos = [srv.poll(t) for t in ts]
+        for t in [t_long] + ts:
+            srv.result(t)
+    # the short ones were admitted and finished while the long one was running
+    assert all(i["t_admit"] < il["t_done"] for i in infos)
+    assert all(i["t_done"] < il["t_done"] for i in infos)
+
+
+def test_failures_reported_per_ticket(L):
+    """A request that goes non-finite (linear material, nu = 0.45, loaded:
+    beyond the scheme's stability) fails alone with LBS_EUNSTABLE; the
+    request beside it completes."""
+    bad = I.tension(32, 32, 1500, ramp=50, model="le", nu=0.45)
+    good = I.tension(32, 32, 100, ramp=50, model="nh")
+    with L.Server(precision="fp64", chunk=32) as srv:
+        tb = srv.submit(bad)
+        tg = srv.submit(good)
+        srv.drain(120)
+        assert srv.poll(tg)["state"] == "done"
+        info = srv.poll(tb)
+        assert info["state"] == "failed" and info["error"] == L.EUNSTABLE
+        assert srv.result(tg)[3] == L.OK
+        assert srv.result(tb)[3] == L.EUNSTABLE
+    with pytest.raises(L.LbsError) as e:
+        with L.Server(precision="fp32", hbm_budget=1 << 20) as srv:
+            srv.submit(I.tension(1024, 1024, 10))
+    assert e.value.code == L.ENOMEM
