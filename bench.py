@@ -145,7 +145,9 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
-def time_precision(L, I, torch, precision, n, steps, warmup, stream, v0dev):
+def time_precision(L, I, torch, precision, n, steps, warmup, stream, v0dev, uref=None):
+    """Time one precision on the roofline lattice; with uref (the FP64 u after
+    warmup + steps iterations) also state its error."""
     case = I.roofline(n=n, nsteps=steps, precision=precision)
     sim = L.Simulation(case, stream=stream)
     sim.set_initial(None, v0dev)
@@ -157,10 +159,87 @@ def time_precision(L, I, torch, precision, n, steps, warmup, stream, v0dev):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    u = torch.empty((n, n, 2), dtype=torch.float64, device=v0dev.device)
+    sim.fields_device(u, None, None)
+    sim.sync()
     sim.close()
     bpn = BYTES_PER_NODE[precision]
-    return {"mlups": n * n / (ms * 1e-3) / 1e6, "ms_per_step": ms, "gbs": bpn * n * n / (ms * 1e-3) / 1e9,
-            "bytes_per_node": bpn}
+    out = {"mlups": n * n / (ms * 1e-3) / 1e6, "ms_per_step": ms, "gbs": bpn * n * n / (ms * 1e-3) / 1e9,
+           "bytes_per_node": bpn, "iterations": warmup + steps}
+    if uref is not None:
+        out["u_rel_err_vs_fp64"] = float((u - uref).abs().max() / uref.abs().max())
+    return out, u
+
+
+def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: float = 1.5):
+    """Batched serving vs one-at-a-time FP64 on a seeded trace of mixed
+    requests (sizes log-uniform 32..1024 x 32..512, SVK or neo-Hooke, nu in
+    [0, 0.45], tension / shear / tip-pulse loads, iterations log-uniform
+    1k..50k scaled by steps_scale).
+
+    The one-at-a-time FP64 baseline runs every request alone (create, step,
+    fetch fields, destroy) and records its service time; its FIFO queue under
+    the arrival times is then exact: done_i = max(arrival_i, done_{i-1}) +
+    service_i.  Arrivals are Poisson at `load` times that baseline's capacity.
+    The FP32 server then receives the same arrivals in real time."""
+    import threading
+    trace = I.serving_trace(n_requests, seed=seed, rate=1.0)
+    cases = [c.replace(nsteps=max(100, int(round(c.nsteps * steps_scale)))) for _, c in trace]
+    work = [c.nx * c.ny * c.nsteps for c in cases]
+    # one at a time, FP64
+    service = []
+    failed_seq = 0
+    for c in cases:
+        t0 = time.perf_counter()
+        try:
+            with L.Simulation(c.replace(precision="fp64")) as s:
+                s.step(c.nsteps)
+                s.sync()
+                s.fields(True, True, True)
+        except L.LbsError:
+            failed_seq += 1
+        service.append(time.perf_counter() - t0)
+    capacity = len(cases) / sum(service)
+    rate = load * capacity
+    gaps = [a for a, _ in trace]
+    arrivals = [t / rate for t in gaps]  # the trace was drawn at rate 1
+    done, t = [], 0.0
+    for a, sv in zip(arrivals, service):
+        t = max(a, t) + sv
+        done.append(t)
+    seq_ttr = [d - a for d, a in zip(done, arrivals)]
+    seq_mlups = sum(work) / (done[-1] - arrivals[0]) / 1e6
+    # batched, FP32
+    srv = L.Server(precision="fp32", chunk=64)
+    tickets = [None] * len(cases)
+    t_start = time.perf_counter()
+
+    def submitter():
+        for i, (a, c) in enumerate(zip(arrivals, cases)):
+            delay = a - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = srv.submit(c.replace(precision="fp32"))
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    srv.drain(-1)
+    infos = [srv.poll(tk) for tk in tickets]
+    stats = srv.stats()
+    for tk in tickets:
+        srv.result(tk)
+    srv.close()
+    ttr = [i["t_done"] - i["t_submit"] for i in infos]
+    span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+    q = lambda xs, p: sorted(xs)[min(len(xs) - 1, int(round(p * (len(xs) - 1))))]
+    return {"requests": len(cases), "steps_scale": steps_scale, "offered_load_x_fp64_capacity": load,
+            "arrival_rate_per_s": rate, "node_updates": sum(work),
+            "batched_fp32": {"aggregate_mlups": sum(work) / span / 1e6, "p50_s": q(ttr, 0.5), "p99_s": q(ttr, 0.99),
+                             "failed": int(sum(i["state"] == "failed" for i in infos)),
+                             "launches": stats["launches"], "busy_s": stats["busy_seconds"]},
+            "sequential_fp64": {"aggregate_mlups": seq_mlups, "p50_s": q(seq_ttr, 0.5), "p99_s": q(seq_ttr, 0.99),
+                                "failed": failed_seq, "service_s": sum(service)}}
 
 
 def main():
@@ -177,6 +256,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--serving-steps-scale", type=float, default=0.1)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -281,9 +363,16 @@ def main():
     if not args.no_variants:
         variants = {}
         v0 = I.grf_velocity(case, device=dev)
-        for p in ("fp64", "fp32", "fp16s"):
-            variants[p] = time_precision(L, I, torch, p, n, max(10, K // 10), W, stream, v0)
-        del v0
+        ks = max(10, K // 10)
+        variants["fp64"], uref = time_precision(L, I, torch, "fp64", n, ks, W, stream, v0)
+        for p in ("fp32", "fp16s"):
+            variants[p], _ = time_precision(L, I, torch, p, n, ks, W, stream, v0, uref)
+        del v0, uref
+        torch.cuda.empty_cache()
+
+    serve = None
+    if not args.no_serving and rank == 0:
+        serve = serving(L, I, args.serving_requests, args.serving_steps_scale)
 
     if world > 1:
         dist.barrier()
@@ -300,7 +389,7 @@ def main():
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "l2": f"state {bpn * cells / 1e9:.1f} GB per lattice, larger than L2 (no flush needed)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "precisions": variants}
+            "precisions": variants, "serving": serve}
     print(json.dumps(line), flush=True)
 
 
