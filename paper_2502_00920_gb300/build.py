@@ -34,11 +34,15 @@ def _sources():
         os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
 
 
+STEP_KERNEL_SOURCES = ["lbs_device.cuh", "lbs_internal.h", "kernels_fp64.cu", "kernels_fp32.cu", "kernels_fp16.cu"]
+
+
 def source_hash() -> str:
-    """Hash of the library sources (identifies the kernels a profile was taken on)."""
+    """Hash of the sources of the step kernels (identifies the kernels a
+    profile was taken on)."""
     import hashlib
     h = hashlib.sha256()
-    for path in sorted(_sources()):
+    for path in [os.path.join(CSRC, f) for f in STEP_KERNEL_SOURCES]:
         if os.path.exists(path):
             h.update(os.path.basename(path).encode())
             h.update(open(path, "rb").read())
