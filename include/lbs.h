@@ -161,6 +161,33 @@ int lbs_fields(lbs_handle *h, double *u, double *v, double *P);
 /* As lbs_fields into caller-owned DEVICE buffers; asynchronous. */
 int lbs_fields_device(lbs_handle *h, double *u, double *v, double *P);
 
+/* As lbs_fields, but without allocating device memory.  (The paper has no
+ * counterpart; this is a property of the library.)  lbs_fields stages the
+ * output in device temporaries the size of the whole lattice, allocated and
+ * freed on every call.  Some callers cannot do that: a process whose device
+ * memory is already taken (a server whose resident lattices fill its HBM
+ * budget, or a framework's caching allocator holding most of the free
+ * memory) would get LBS_ENOMEM for exactly the large lattices whose results
+ * matter, and a caller with a latency budget cannot afford cudaFree, which
+ * waits for the whole device.  This entry point instead copies the fields
+ * out a block of rows at a time through one fixed staging array of 8 MiB
+ * (2^20 doubles) in device memory, a file-scope static that every GPU which
+ * loads the library holds until the process exits.  It calls no cudaMalloc
+ * or cudaFree.
+ *  - Limit: one row of the requested fields must fit the array, i.e.
+ *    (2 [u] + 2 [v] + 4 [P]) * nx <= 2^20 doubles (nx <= 131072 with all
+ *    three); larger rows are rejected with LBS_EINVAL.
+ *  - The first call on a device (with that device current, as for every
+ *    call on the handle) looks up the array's device address; make that
+ *    first call before any stream capture.
+ *  - Every call on a device shares the one array, which keeps the last
+ *    call's contents; each call overwrites every entry it copies out, so
+ *    nothing needs clearing.  Calls that overlapped on the GPU would race on
+ *    it: the library serialises calls with a process-wide lock and each call
+ *    returns only after its copies finished, so they do not overlap.
+ * Host buffers and layouts as lbs_fields (any may be NULL); synchronous. */
+int lbs_fields_static(lbs_handle *h, double *u, double *v, double *P);
+
 /* Displacements of n probe nodes idx[i] = y * nx + x into host out[2 n].
  * Synchronous. */
 int lbs_probe(lbs_handle *h, int32_t n, const int32_t *idx, double *out);

@@ -1,0 +1,160 @@
+// lbs_fields_static: field output without device allocation.
+//
+// lbs_fields stages u, v and P in device temporaries the size of the whole
+// lattice (cudaMalloc / cudaFree on every call; up to 17 GB for a 16384^2
+// lattice).  This variant stages them through one fixed 8 MiB array in device
+// memory, a row block at a time, so a call allocates nothing.  The kernel is a
+// variant of the field-output kernel that writes only the rows of one block.
+#include <mutex>
+
+#include "lbs_device.cuh"
+#include "lbs_internal.h"
+
+namespace lbs {
+namespace {
+
+// staging for the row blocks; every GPU that loads the library holds it
+constexpr size_t kStageDoubles = (size_t)1 << 20;  // 8 MiB
+static __device__ __align__(256) double g_fields_stage[kStageDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_stage_mu;
+double *g_stage_ptr[kMaxDevices] = {};
+
+// u, v, P of rows [y_lo, y_hi) into dense row-block arrays (x fastest)
+template <class C>
+__global__ void __launch_bounds__(C::NT) fields_rows_kernel(const Params P, const typename C::gs *g,
+                                                            const typename C::us *u, int y_lo, int y_hi, double *uo,
+                                                            double *vo, double *Po) {
+  using R = typename C::real;
+  __shared__ typename C::Smem sm;
+  const int x0 = blockIdx.x * C::TX, y0 = (y_lo / C::TY + blockIdx.y) * C::TY;
+  load_r2_from_state<C>(sm, P, u, x0, y0);
+  __syncthreads();
+  phase_n<C, true>(sm, P, x0, y0, (R *)nullptr);
+  __syncthreads();
+  const size_t plane = (size_t)P.ny * P.pitch;
+  const R idx_ = (R)P.inv_dx, inv = (R)ldexp(1.0, -P.gshift), mu = (R)P.mu;
+  const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
+  for (int i = 0; i < C::CPT; ++i) {
+    const int lx = tx, ly = ty + i * C::NTY, x = x0 + lx, y = y0 + ly;
+    if (x >= P.nx || y < y_lo || y >= y_hi) continue;
+    const size_t o = (size_t)(y - y_lo) * P.nx + x, idx = (size_t)y * P.pitch + x;
+    const double2 uv = u_value(sm.u[ly + 2][lx + 2]);
+    if (uo) {
+      uo[2 * o] = uv.x;
+      uo[2 * o + 1] = uv.y;
+    }
+    if (vo) {
+      R Sx, Sy;
+      Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
+      Sx += (R)(P.rho0 * P.body[0]);
+      Sy += (R)(P.rho0 * P.body[1]);
+      R m1x = 0, m1y = 0;
+      for (int q = 1; q < 9; ++q) {
+        const R gq = gload(g, q * plane + idx, inv);
+        m1x += R(ex(q)) * gq;
+        m1y += R(ey(q)) * gq;
+      }
+      const double hdt = 0.5 * P.dt;
+      vo[2 * o] = (P.c * (double)m1x - hdt * (double)Sx) / P.rho0;
+      vo[2 * o + 1] = (P.c * (double)m1y - hdt * (double)Sy) / P.rho0;
+    }
+    if (Po) {
+      R H[4];
+      Fd<C, true>::grad(sm, P, lx + 1, ly + 1, x, y, idx_, H);
+      const R trH = H[0] + H[3];
+      Po[4 * o + 0] = (double)(sm.n[0][ly + 1][lx + 1] + mu * (R(2) * H[0] + trH));
+      Po[4 * o + 1] = (double)(sm.n[1][ly + 1][lx + 1] + mu * (H[1] + H[2]));
+      Po[4 * o + 2] = (double)(sm.n[2][ly + 1][lx + 1] + mu * (H[1] + H[2]));
+      Po[4 * o + 3] = (double)(sm.n[3][ly + 1][lx + 1] + mu * (R(2) * H[3] + trH));
+    }
+  }
+}
+
+template <class Pr>
+cudaError_t launch_rows(const Params &P, const void *g, const void *u, int y_lo, int y_hi, double *uo, double *vo,
+                        double *Po, cudaStream_t st) {
+  using C = Cfg<Pr, 32, 16, 8>;
+  const int b_first = y_lo / C::TY, b_last = (y_hi - 1) / C::TY;
+  dim3 grid((P.nx + C::TX - 1) / C::TX, b_last - b_first + 1);
+  fields_rows_kernel<C><<<grid, C::NT, 0, st>>>(P, (const typename C::gs *)g, (const typename C::us *)u, y_lo, y_hi,
+                                                uo, vo, Po);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace lbs
+
+extern "C" int lbs_fields_static(lbs_handle *h, double *u, double *v, double *P) {
+  using namespace lbs;
+  if (!h) {
+    set_error("null handle");
+    return LBS_EINVAL;
+  }
+  const int nx = h->P.nx, ny = h->P.ny;
+  const int wu = u ? 2 : 0, wv = v ? 2 : 0, wp = P ? 4 : 0;
+  const size_t per_row = (size_t)(wu + wv + wp) * nx;
+  if (per_row == 0) return LBS_OK;
+  if (per_row > kStageDoubles) {
+    set_error("lbs_fields_static: one row of " + std::to_string(nx) + " nodes needs " + std::to_string(per_row) +
+              " doubles of staging, more than the static 8 MiB array holds (" + std::to_string(kStageDoubles) +
+              "); use lbs_fields");
+    return LBS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_error("lbs_fields_static: no usable current device");
+    return LBS_ECUDA;
+  }
+  if (!g_stage_ptr[dev]) {
+    // the array's name is a host-side stand-in; its device address is looked
+    // up once per device, with that device current
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_fields_stage);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("lbs_fields_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      return LBS_ECUDA;
+    }
+    g_stage_ptr[dev] = (double *)p;
+  }
+  double *stage = g_stage_ptr[dev];
+  const int rows = (int)(kStageDoubles / per_row);
+  for (int y_lo = 0; y_lo < ny; y_lo += rows) {
+    const int y_hi = y_lo + rows < ny ? y_lo + rows : ny;
+    const size_t n = (size_t)(y_hi - y_lo) * nx;
+    double *su = stage, *sv = su + wu * n, *sp = sv + wv * n;
+    cudaError_t le;
+    if (h->precision == LBS_FP64)
+      le = launch_rows<F64>(h->P, h->g[h->parity], h->u[h->parity], y_lo, y_hi, u ? su : nullptr, v ? sv : nullptr,
+                            P ? sp : nullptr, h->stream);
+    else if (h->precision == LBS_FP32)
+      le = launch_rows<F32>(h->P, h->g[h->parity], h->u[h->parity], y_lo, y_hi, u ? su : nullptr, v ? sv : nullptr,
+                            P ? sp : nullptr, h->stream);
+    else
+      le = launch_rows<F16>(h->P, h->g[h->parity], h->u[h->parity], y_lo, y_hi, u ? su : nullptr, v ? sv : nullptr,
+                            P ? sp : nullptr, h->stream);
+    if (le != cudaSuccess) {
+      set_error(std::string("lbs_fields_static: launch: ") + cudaGetErrorString(le));
+      return LBS_ECUDA;
+    }
+    h->launches += 1;
+    // the next block's kernel follows these copies on the same stream
+    if ((u && cudaMemcpyAsync(u + (size_t)2 * y_lo * nx, su, 2 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream) != cudaSuccess) ||
+        (v && cudaMemcpyAsync(v + (size_t)2 * y_lo * nx, sv, 2 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream) != cudaSuccess) ||
+        (P && cudaMemcpyAsync(P + (size_t)4 * y_lo * nx, sp, 4 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream) != cudaSuccess)) {
+      set_error("lbs_fields_static: copy to host failed");
+      return LBS_ECUDA;
+    }
+  }
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+    set_error(std::string("lbs_fields_static: ") + cudaGetErrorString(e));
+    return LBS_ECUDA;
+  }
+  return LBS_OK;
+}

@@ -77,6 +77,7 @@ SIGNATURES = {
     "lbs_sync": (ctypes.c_int, [_vp]),
     "lbs_fields": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
     "lbs_fields_device": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbs_fields_static": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
     "lbs_probe": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _dp]),
     "lbs_monitor": (ctypes.c_int, [_vp, ctypes.POINTER(Monitors)]),
     "lbs_set_monitor_interval": (ctypes.c_int, [_vp, ctypes.c_int64]),
@@ -332,6 +333,14 @@ class Simulation:
             else:
                 out.append(np.empty((ny, nx, w)) if want else None)
         check(lib().lbs_fields(self._h, *[_ptr(a) if a is not None else None for a in out]))
+        return tuple(out)
+
+    def fields_static(self, u=True, v=True, P=True):
+        """As fields(), through lbs_fields_static: no device memory is
+        allocated (rows are staged through a fixed 8 MiB device array)."""
+        ny, nx = self.case.ny, self.case.nx
+        out = [np.empty((ny, nx, w)) if want else None for want, w in ((u, 2), (v, 2), (P, 4))]
+        check(lib().lbs_fields_static(self._h, *[_ptr(a) if a is not None else None for a in out]))
         return tuple(out)
 
     def fields_device(self, u=None, v=None, P=None):
