@@ -263,14 +263,12 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2502_00920_gb300 import replicas as RP
+    rank, world, local = RP.ranks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
     import torch
-    import torch.distributed as dist
     from paper_2502_00920_gb300 import build as B
     B.build()
     from paper_2502_00920_gb300 import inputs as I
@@ -278,12 +276,10 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        dist.init_process_group("gloo")
+    RP.init(world)
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        RP.barrier(world)
 
     n, K, W = args.n, args.steps, args.warmup
     case = I.roofline(n=n, nsteps=args.e2e_steps, precision=args.precision, seed=5 + rank)
@@ -308,12 +304,9 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = sim.launch_count - launches0
     sim.sync()  # raises if a monitor saw a non-finite value
-    t = torch.tensor([ms], dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t[0])
+    ms_max = RP.max_over_ranks(ms, world)
     cells = n * n
-    value = world * cells * K / (ms_max * 1e-3) / 1e6
+    value = RP.aggregate_rate(cells * K, ms_max * 1e-3, world) / 1e6
 
     # roofline of the step kernels: algorithmic bytes per launch pair / its
     # average duration in the timed region (events on the launching stream)
@@ -349,12 +342,10 @@ def main():
         sim.fields(uo.numpy(), vo.numpy(), False)
         te = time.perf_counter() - t0
         sim.close()
-        te_t = torch.tensor([te], dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * cells * E / float(te_t[0]) / 1e6, "unit": "MLUPS",
+        te_max = RP.max_over_ranks(te, world)
+        e2e = {"value": RP.aggregate_rate(cells * E, te_max, world) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": vh.numel() * 8 / E, "d2h_bytes_per_step": (uo.numel() + vo.numel()) * 8 / E,
-               "job": f"set_initial(host v0) + {E} iterations + fields(host u, v)", "seconds": float(te_t[0])}
+               "job": f"set_initial(host v0) + {E} iterations + fields(host u, v)", "seconds": te_max}
         del vh, uo, vo
     else:
         del v0
@@ -374,8 +365,7 @@ def main():
     if not args.no_serving and rank == 0:
         serve = serving(L, I, args.serving_requests, args.serving_steps_scale)
 
-    if world > 1:
-        dist.barrier()
+    barrier()
     if rank != 0:
         return
     cpu = None
