@@ -48,7 +48,7 @@ bool tma_maps(const Params &p, int v, const void *g, const void *u, void *og, vo
 }
 
 const Launchers kL = {kVariants,
-                      4,
+                      1 << 4,
                       3,  // default: the fastest on the 16384^2 roofline lattice
                       shape,
                       step,

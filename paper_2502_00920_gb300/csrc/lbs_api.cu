@@ -280,7 +280,7 @@ int launch_monitor_async(lbs_handle *h) {
 int select_variant(lbs_handle *h, int variant) {
   bool tma = h->L->tma_maps(h->P, variant, h->g[0], h->u[0], &h->tm_g[0], &h->tm_u[0]);
   if (tma) tma = h->L->tma_maps(h->P, variant, h->g[1], h->u[1], &h->tm_g[1], &h->tm_u[1]);
-  if (!tma && variant == h->L->tma_index)
+  if (!tma && ((h->L->tma_mask >> variant) & 1))
     return fail(LBS_ECUDA, "TMA descriptors could not be built for tile variant " + std::to_string(variant));
   h->tma = tma;
   h->variant = variant;
@@ -366,7 +366,7 @@ int lbs_tile_variant_kind(int32_t precision, int32_t variant) {
   if (precision < LBS_FP64 || precision > LBS_FP16S) return fail(LBS_EINVAL, "unknown precision");
   const Launchers &L = launchers_for(precision);
   if (variant < 0 || variant >= L.nvariants) return fail(LBS_EINVAL, "unknown tile variant");
-  return variant == L.tma_index ? 1 : 0;
+  return (L.tma_mask >> variant) & 1;
 }
 
 int lbs_tile_variants(int32_t precision, int32_t *count, int32_t *tx, int32_t *ty) {

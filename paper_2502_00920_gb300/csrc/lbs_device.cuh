@@ -60,10 +60,12 @@ struct F16 {
 
 __device__ __forceinline__ double gload(const double *p, size_t i, double) { return __ldg(p + i); }
 __device__ __forceinline__ float gload(const float *p, size_t i, float) { return __ldg(p + i); }
-__device__ __forceinline__ float gload(const __half *p, size_t i, float inv) { return __half2float(__ldg(p + i)) * inv; }
+// FP16 storage: the kernels work in units of g * 2^gshift (exact power-of-two
+// scaling), so loads and stores only convert
+__device__ __forceinline__ float gload(const __half *p, size_t i, float) { return __half2float(__ldg(p + i)); }
 __device__ __forceinline__ void gstore(double *p, size_t i, double v, double) { p[i] = v; }
 __device__ __forceinline__ void gstore(float *p, size_t i, float v, float) { p[i] = v; }
-__device__ __forceinline__ void gstore(__half *p, size_t i, float v, float s) { p[i] = __float2half_rn(v * s); }
+__device__ __forceinline__ void gstore(__half *p, size_t i, float v, float) { p[i] = __float2half_rn(v); }
 
 // difference of two displacement records, as the compute type
 __device__ __forceinline__ void udiff(const double2 &a, const double2 &b, double &dx, double &dy) {
@@ -213,13 +215,14 @@ __device__ inline void edge_value(const Params &P, int e, int64_t k, double out[
 // the two shear entries.
 template <class R>
 __device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t k, const R g0[9], unsigned mask,
-                           R f[9]) {
+                           R f[9], R gsc) {
   int xw = -1, yw = -1;
   if (!P.per_x) xw = (x == 0) ? kLeft : ((x == P.nx - 1) ? kRight : -1);
   if (!P.per_y) yw = (y == 0) ? kBottom : ((y == P.ny - 1) ? kTop : -1);
   const bool xn = xw >= 0 && P.etype[xw] == LBS_NEUMANN;
   const bool yn = yw >= 0 && P.etype[yw] == LBS_NEUMANN;
-  const R ics2 = (R)P.inv_cs2;
+  // Pi*/cs^2 from N and T* is brought into the units of g (times gsc)
+  const R ics2 = (R)P.inv_cs2 * gsc;
   // own moments (collision leaves r and Pi unchanged): r, A = Pi / cs^2 = 3 sum e e g
   R r = 0, mxx = 0, mxy = 0, myy = 0;
 #pragma unroll
@@ -249,7 +252,7 @@ __device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t 
     Ayy_y = (Nn[3] - s * (R)T[1]) * ics2;
     axy_y = (Nn[1] - s * (R)T[0]) * ics2;
   }
-  const R cj = (R)(P.c * P.inv_cs2);
+  const R cj = (R)(P.c * P.inv_cs2) * gsc;
 #pragma unroll
   for (int q = 1; q < 9; ++q) {
     if (!(mask & (1u << q))) continue;
@@ -384,7 +387,7 @@ __device__ __forceinline__ bool locate(const Params &P, int &x, int &y) {
 template <class Pr, bool EDGE>
 __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *__restrict__ g, const typename Pr::real *bnd,
                                        int x, int y, int64_t k, typename Pr::real inv, typename Pr::real f[9],
-                                       typename Pr::real &gx, typename Pr::real &gy) {
+                                       typename Pr::real &gx, typename Pr::real &gy, typename Pr::real gsc) {
   using R = typename Pr::real;
   const size_t plane = (size_t)P.ny * P.pitch;
   const size_t idx = (size_t)y * P.pitch + x;
@@ -417,7 +420,7 @@ __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *_
         f[q] = gload(g, q * plane + (size_t)sy * P.pitch + sx, inv);
       }
     }
-    if (mask) wall_rules<R>(P, bnd, x, y, k, g0, mask, f);
+    if (mask) wall_rules<R>(P, bnd, x, y, k, g0, mask, f, gsc);
   }
   gx = (g0[1] - g0[3]) + (g0[5] - g0[6]) + (g0[8] - g0[7]);
   gy = (g0[2] - g0[4]) + (g0[5] - g0[8]) + (g0[6] - g0[7]);
@@ -525,8 +528,9 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
   us *__restrict__ uo = (us *)S.u_out;
   const R *bnd = (const R *)S.b_in;
   const int64_t k = EDGE ? (*S.kptr + S.koff) : 0;
+  // g is held in units of g * 2^gshift (1 unless FP16 storage)
   const R inv = (R)ldexp(1.0, -P.gshift), scl = (R)ldexp(1.0, P.gshift);
-  const R kap = (R)P.kappa;
+  const R kap = (R)P.kappa * inv;
   const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
 
   // phase 1a: own nodes (keep the streamed populations).  In a tile that
@@ -540,7 +544,7 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     int x = x0 + lx, y = y0 + ly;
     if (EDGE && !locate(P, x, y)) continue;
     R gxm, gym;
-    gather<typename C::PrT, EDGE>(P, g, bnd, x, y, k, inv, f[i], gxm, gym);
+    gather<typename C::PrT, EDGE>(P, g, bnd, x, y, k, inv, f[i], gxm, gym, scl);
     const R fx = (f[i][1] - f[i][3]) + (f[i][5] - f[i][6]) + (f[i][8] - f[i][7]);
     const R fy = (f[i][2] - f[i][4]) + (f[i][5] - f[i][8]) + (f[i][6] - f[i][7]);
     sm.u[ly + 2][lx + 2] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
@@ -552,7 +556,7 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     int x = x0 - 2 + rx, y = y0 - 2 + ry;
     if (EDGE && !locate(P, x, y)) continue;
     R ff[9], gxm, gym;
-    gather<typename C::PrT, EDGE>(P, g, bnd, x, y, k, inv, ff, gxm, gym);
+    gather<typename C::PrT, EDGE>(P, g, bnd, x, y, k, inv, ff, gxm, gym, scl);
     const R fx = (ff[1] - ff[3]) + (ff[5] - ff[6]) + (ff[8] - ff[7]);
     const R fy = (ff[2] - ff[4]) + (ff[5] - ff[8]) + (ff[6] - ff[7]);
     sm.u[ry][rx] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
@@ -573,7 +577,7 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     Fd<C, EDGE>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
     Sx += sbx;
     Sy += sby;
-    collide<R>(f[i], Sx, Sy, omega, sigma);
+    collide<R>(f[i], Sx * scl, Sy * scl, omega, sigma);
     const size_t idx = (size_t)y * P.pitch + x;
 #pragma unroll
     for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[i][q], scl);
@@ -820,11 +824,12 @@ __global__ void __launch_bounds__(C::NT) step_tma_kernel(const Params P, const S
     return;
   }
 
+  // g is held in units of g * 2^gshift (1 unless FP16 storage)
   const R inv = (R)ldexp(1.0, -P.gshift), scl = (R)ldexp(1.0, P.gshift);
-  const R kap = (R)P.kappa;
+  const R kap = (R)P.kappa * inv;
   auto G = [&](int q, int r, int c) -> R {
     const gs v = sg[((size_t)q * T::GH + r) * T::GW + c];
-    if constexpr (sizeof(gs) == 2) return __half2float(v) * inv;
+    if constexpr (sizeof(gs) == 2) return __half2float(v);
     else return (R)v;
   };
   // phase 1: u(t+dt) on R2, in place (R2 position (cx, cy) = node (x0-2+cx, y0-2+cy);
@@ -885,7 +890,7 @@ __global__ void __launch_bounds__(C::NT) step_tma_kernel(const Params P, const S
     auto n = [&](int m, int yy, int xx) -> R { return snb[(m * H1 + yy) * W1 + xx]; };
     const R Sx = (n(0, ry, rx + 1) - n(0, ry, rx - 1)) * hdx + (n(1, ry + 1, rx) - n(1, ry - 1, rx)) * hdx + sbx;
     const R Sy = (n(2, ry, rx + 1) - n(2, ry, rx - 1)) * hdx + (n(3, ry + 1, rx) - n(3, ry - 1, rx)) * hdx + sby;
-    collide<R>(f, Sx, Sy, omega, sigma);
+    collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
     const size_t idx = (size_t)(y0 + ly) * P.pitch + (x0 + lx);
 #pragma unroll
     for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[q], scl);
@@ -904,6 +909,187 @@ cudaError_t launch_step_tma(const Params &P, const StepPtrs &S, cudaStream_t st)
     if (!S.tm_g || !S.tm_u) return cudaErrorInvalidValue;
     step_tma_kernel<C><<<dim3(ni, nj), C::NT, T::SMEM, st>>>(P, S, *(const CUtensorMap *)S.tm_g,
                                                                *(const CUtensorMap *)S.tm_u, a_lo, b_lo);
+  }
+  const int nedge = ntx * nty - ni * nj;
+  if (nedge > 0) step_edge_kernel<C><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+  return cudaGetLastError();
+}
+
+// Persistent variant: each block walks interior tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... with two shared-memory stages, prefetching tile
+// t + gridDim.x by TMA while it computes tile t.
+template <class C>
+struct Tma2Cfg {
+  using T = TmaCfg<C>;
+  static constexpr size_t STAGE = T::OFF_N;  // g and u of one tile (128-aligned)
+  static constexpr size_t OFF_N = 2 * STAGE;
+  static constexpr size_t OFF_BAR = OFF_N + (T::N_BYTES + 15) / 16 * 16;
+  static constexpr size_t SMEM = OFF_BAR + 32;
+};
+
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <class C>
+__device__ __forceinline__ void tma2_issue(unsigned char *stage, uint64_t *bar, const CUtensorMap &tm_g,
+                                           const CUtensorMap &tm_u, int x0, int y0) {
+  using T = TmaCfg<C>;
+  mbar_expect_tx(bar, (uint32_t)(T::G_BYTES + T::U_BYTES));
+  tma_load_3d(stage, &tm_g, x0 - T::XO, y0 - 3, 0, bar);
+  tma_load_2d(stage + T::OFF_U, &tm_u, T::UEL * (x0 - 2), y0 - 2, bar);
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::NT) step_tma2_kernel(const Params P, const StepPtrs S,
+                                                          const __grid_constant__ CUtensorMap tm_g,
+                                                          const __grid_constant__ CUtensorMap tm_u, int a_lo, int b_lo,
+                                                          int ni, int ntiles) {
+  using T = TmaCfg<C>;
+  using T2 = Tma2Cfg<C>;
+  using R = typename C::real;
+  using us = typename C::us;
+  using gs = typename C::gs;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  R *snb = (R *)(dsm + T2::OFF_N);
+  uint64_t *bar = (uint64_t *)(dsm + T2::OFF_BAR);  // bar[0], bar[1]
+  auto tile_xy = [&](int t, int &x0, int &y0) {
+    x0 = (a_lo + t % ni) * C::TX;
+    y0 = (b_lo + t / ni) * C::TY;
+  };
+  int t = blockIdx.x;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    if (t < ntiles) {
+      int x0, y0;
+      tile_xy(t, x0, y0);
+      tma2_issue<C>(dsm, &bar[0], tm_g, tm_u, x0, y0);
+    }
+  }
+  __syncthreads();
+  const R inv = (R)ldexp(1.0, -P.gshift), scl = (R)ldexp(1.0, P.gshift);
+  const R kap = (R)P.kappa * inv;
+  const size_t plane = (size_t)P.ny * P.pitch;
+  const R omega = (R)P.omega, sigma = (R)P.sigma, hdx = R(0.5) * (R)P.inv_dx;
+  const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
+  const R lam = (R)P.lam, mu = (R)P.mu;
+  gs *__restrict__ go = (gs *)S.g_out;
+  us *__restrict__ uo = (us *)S.u_out;
+  constexpr int W1 = C::TX + 2, H1 = C::TY + 2;
+  const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
+
+  for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
+    const int s = i & 1;
+    unsigned char *stage = dsm + s * T2::STAGE;
+    gs *sg = (gs *)stage;
+    us *su = (us *)(stage + T::OFF_U);
+    // prefetch the next tile into the other stage (its previous tile is done:
+    // the barrier at the end of the last iteration)
+    const int tn = t + gridDim.x;
+    if (threadIdx.x == 0 && tn < ntiles) {
+      int x1, y1;
+      tile_xy(tn, x1, y1);
+      fence_async_shared();
+      tma2_issue<C>(dsm + (s ^ 1) * T2::STAGE, &bar[s ^ 1], tm_g, tm_u, x1, y1);
+    }
+    int ok = 0;
+    const uint32_t parity = (uint32_t)((i >> 1) & 1);
+    for (uint32_t it = 0; it < kMaxPolls; ++it)
+      if (mbar_try_wait(&bar[s], parity)) {
+        ok = 1;
+        break;
+      }
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        if (S.err) atomicExch(S.err, 1);
+        // let the prefetch into the other stage land before leaving
+        if (tn < ntiles)
+          for (uint32_t it = 0; it < kMaxPolls; ++it)
+            if (mbar_try_wait(&bar[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1))) break;
+      }
+      return;
+    }
+    int x0, y0;
+    tile_xy(t, x0, y0);
+    auto G = [&](int q, int r, int c) -> R {
+      const gs v = sg[((size_t)q * T::GH + r) * T::GW + c];
+      if constexpr (sizeof(gs) == 2) return __half2float(v);
+      else return (R)v;
+    };
+    // phase 1: u(t+dt) on R2, in place
+    for (int e = threadIdx.x; e < T::UW * T::UH; e += C::NT) {
+      const int cx = e % T::UW, cy = e / T::UW;
+      const int gr = cy + 1, gc = cx + T::XO - 2;
+      R p[9], o[9];
+#pragma unroll
+      for (int q = 1; q < 9; ++q) {
+        p[q] = G(q, gr - ey(q), gc - ex(q));
+        o[q] = G(q, gr, gc);
+      }
+      const R gx = (o[1] - o[3]) + (o[5] - o[6]) + (o[8] - o[7]);
+      const R gy = (o[2] - o[4]) + (o[5] - o[8]) + (o[6] - o[7]);
+      const R fx = (p[1] - p[3]) + (p[5] - p[6]) + (p[8] - p[7]);
+      const R fy = (p[2] - p[4]) + (p[5] - p[8]) + (p[6] - p[7]);
+      su[e] = uadd(su[e], kap * (gx + fx), kap * (gy + fy));
+    }
+    __syncthreads();
+    // phase 2: N on R1
+    for (int e = threadIdx.x; e < W1 * H1; e += C::NT) {
+      const int rx = e % W1, ry = e / W1;
+      const int c = (ry + 1) * T::UW + (rx + 1);
+      R dxx, dxy, dyx, dyy, H[4], N[4];
+      udiff(su[c + 1], su[c - 1], dxx, dxy);
+      udiff(su[c + T::UW], su[c - T::UW], dyx, dyy);
+      H[0] = dxx * hdx;
+      H[1] = dyx * hdx;
+      H[2] = dxy * hdx;
+      H[3] = dyy * hdx;
+      material<R>(P, lam, mu, H, N);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) snb[(m * H1 + ry) * W1 + rx] = N[m];
+    }
+    __syncthreads();
+    // phase 3: stream, source, collision, store
+#pragma unroll
+    for (int j = 0; j < C::CPT; ++j) {
+      const int lx = tx, ly = ty + j * C::NTY;
+      const int gr = ly + 3, gc = lx + T::XO;
+      R f[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) f[q] = G(q, gr - ey(q), gc - ex(q));
+      const int rx = lx + 1, ry = ly + 1;
+      auto n = [&](int m, int yy, int xx) -> R { return snb[(m * H1 + yy) * W1 + xx]; };
+      const R Sx = (n(0, ry, rx + 1) - n(0, ry, rx - 1)) * hdx + (n(1, ry + 1, rx) - n(1, ry - 1, rx)) * hdx + sbx;
+      const R Sy = (n(2, ry, rx + 1) - n(2, ry, rx - 1)) * hdx + (n(3, ry + 1, rx) - n(3, ry - 1, rx)) * hdx + sby;
+      collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
+      const size_t idx = (size_t)(y0 + ly) * P.pitch + (x0 + lx);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[q], scl);
+      uo[idx] = su[(ly + 2) * T::UW + (lx + 2)];
+    }
+    __syncthreads();  // this stage is free for the prefetch after next
+  }
+}
+
+template <class C>
+cudaError_t launch_step_tma2(const Params &P, const StepPtrs &S, cudaStream_t st) {
+  using T2 = Tma2Cfg<C>;
+  const int ntx = (P.nx + C::TX - 1) / C::TX, nty = (P.ny + C::TY - 1) / C::TY;
+  int a_lo, a_hi, b_lo, b_hi;
+  interior_range(P.nx, P.ny, C::TX, C::TY, a_lo, a_hi, b_lo, b_hi);
+  const int ni = a_hi - a_lo, nj = b_hi - b_lo;
+  if (ni > 0 && nj > 0) {
+    if (!S.tm_g || !S.tm_u) return cudaErrorInvalidValue;
+    static int blocks = 0;
+    if (!blocks) {
+      int dev = 0, sms = 0, per = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_tma2_kernel<C>, C::NT, T2::SMEM);
+      blocks = sms * (per > 0 ? per : 1);
+    }
+    const int ntiles = ni * nj;
+    step_tma2_kernel<C><<<ntiles < blocks ? ntiles : blocks, C::NT, T2::SMEM, st>>>(
+        P, S, *(const CUtensorMap *)S.tm_g, *(const CUtensorMap *)S.tm_u, a_lo, b_lo, ni, ntiles);
   }
   const int nedge = ntx * nty - ni * nj;
   if (nedge > 0) step_edge_kernel<C><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
@@ -945,7 +1131,9 @@ bool make_tma_maps(const Params &P, const void *g, const void *u, void *out_g, v
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return false;
   return cudaFuncSetAttribute(step_tma_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM) ==
-         cudaSuccess;
+             cudaSuccess &&
+         cudaFuncSetAttribute(step_tma2_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Tma2Cfg<C>::SMEM) == cudaSuccess;
 }
 
 // ------------------------------------------------------------------ init / fields
@@ -1009,9 +1197,9 @@ __global__ void __launch_bounds__(C::NT) init_kernel(const Params P, typename C:
       const int e2 = ex(q) * ex(q) + ey(q) * ey(q);
       const R rq = (e2 == 0) ? R(2) * r0 : ((e2 == 1) ? R(0.5) * r0 : -r0);
       const R eAe = R(ex(q) * ex(q)) * Axx + R(2 * ex(q) * ey(q)) * Axy + R(ey(q) * ey(q)) * Ayy;
-      f[q] = wq<R>(q) * (rq + R(ex(q)) * jx + R(ey(q)) * jy + R(1.5) * eAe - R(0.5) * (Axx + Ayy));
+      f[q] = wq<R>(q) * (rq + R(ex(q)) * jx + R(ey(q)) * jy + R(1.5) * eAe - R(0.5) * (Axx + Ayy)) * scl;
     }
-    collide<R>(f, Sx, Sy, (R)P.omega, (R)P.sigma);
+    collide<R>(f, Sx * scl, Sy * scl, (R)P.omega, (R)P.sigma);
     const size_t idx = (size_t)y * P.pitch + x;
     for (int q = 0; q < 9; ++q) gstore(g, q * plane + idx, f[q], scl);
     u[idx] = sm.u[ly + 2][lx + 2];
@@ -1053,8 +1241,8 @@ __global__ void __launch_bounds__(C::NT) fields_kernel(const Params P, const typ
         m1y += R(ey(q)) * gq;
       }
       const double hdt = 0.5 * P.dt;
-      vo[2 * o] = (P.c * (double)m1x - hdt * (double)Sx) / P.rho0;
-      vo[2 * o + 1] = (P.c * (double)m1y - hdt * (double)Sy) / P.rho0;
+      vo[2 * o] = (P.c * (double)(m1x * inv) - hdt * (double)Sx) / P.rho0;
+      vo[2 * o + 1] = (P.c * (double)(m1y * inv) - hdt * (double)Sy) / P.rho0;
     }
     if (Po) {
       R H[4];
@@ -1098,7 +1286,7 @@ __global__ void __launch_bounds__(kMonThreads) monitor_kernel(const Params P, co
     umax = fmax(umax, fmax(fabs(uv.x), fabs(uv.y)));
     double r = 0, ax = 0, ay = 0;
     for (int q = 0; q < 9; ++q) {
-      const double v = (double)gload(g, q * plane + idx, inv);
+      const double v = (double)(gload(g, q * plane + idx, inv) * inv);
       bad += isfinite(v) ? 0.0 : 1.0;
       r += v;
       ax += ex(q) * v;

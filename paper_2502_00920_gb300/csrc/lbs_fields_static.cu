@@ -57,8 +57,9 @@ __global__ void __launch_bounds__(C::NT) fields_rows_kernel(const Params P, cons
         m1y += R(ey(q)) * gq;
       }
       const double hdt = 0.5 * P.dt;
-      vo[2 * o] = (P.c * (double)m1x - hdt * (double)Sx) / P.rho0;
-      vo[2 * o + 1] = (P.c * (double)m1y - hdt * (double)Sy) / P.rho0;
+      // g is held in units of g * 2^gshift (1 unless FP16 storage)
+      vo[2 * o] = (P.c * (double)(m1x * inv) - hdt * (double)Sx) / P.rho0;
+      vo[2 * o + 1] = (P.c * (double)(m1y * inv) - hdt * (double)Sy) / P.rho0;
     }
     if (Po) {
       R H[4];

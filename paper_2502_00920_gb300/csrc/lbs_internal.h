@@ -72,7 +72,7 @@ struct BatchTile {
 // shape (0 = default).  Return a cudaError_t of the launch.
 struct Launchers {
   int nvariants;
-  int tma_index;  // the variant whose interior tiles are staged by TMA
+  int tma_mask;   // bit v set: variant v stages its interior tiles by TMA
   int default_variant;
   TileShape (*shape)(int variant);
   cudaError_t (*step)(const Params &p, const StepPtrs &s, int variant, cudaStream_t st);
