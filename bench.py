@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -242,6 +244,125 @@ def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: floa
                                 "failed": failed_seq, "service_s": sum(service)}}
 
 
+def suite(args):
+    """Every benchmark configuration in every precision: MLUPS, and the error
+    on u (and P) against the oracle where it can run the whole history, else
+    against the GPU's own FP64 (itself checked against the oracle on a prefix
+    and on windows).  Prints one JSON line per result."""
+    import torch
+    from oracle import oracle as O
+    from paper_2502_00920_gb300 import inputs as I
+    from paper_2502_00920_gb300 import lbs as L
+
+    dev = torch.device("cuda")
+    rel = lambda a, b: float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+    def emit(**kw):
+        print(json.dumps(kw), flush=True)
+
+    def gpu_run(case, steps, monitor=0, probe=None, every=100):
+        sim = L.Simulation(case, monitor_interval=monitor)
+        hist = []
+        t0 = time.perf_counter()
+        k, unstable = 0, None
+        try:
+            while k < steps:
+                n = min(every if probe is not None else steps, steps - k)
+                sim.step(n)
+                k += n
+                if probe is not None:
+                    hist.append(sim.probe([probe])[0].copy())
+            sim.sync()
+        except L.LbsError as e:
+            unstable = sim.unstable_iteration if e.code == L.EUNSTABLE else str(e)
+        dt = time.perf_counter() - t0
+        out = sim.fields()
+        sim.close()
+        return out, dt, unstable, np.array(hist)
+
+    # tension 32x32, neo-Hooke, 2000 iterations
+    case = I.tension()
+    ora = O.OracleSim(case)
+    ora_hist, k_nan = {}, None
+    for k in range(0, 2000, 50):
+        ora.step(50)
+        if k + 50 in (1000, 2000):
+            ora_hist[k + 50] = ora.fields()
+        if k_nan is None and not np.isfinite(ora.fields()[0]).all():
+            k_nan = k + 50
+    for prec in ("fp64", "fp32", "fp16s"):
+        for steps in (1000, 2000):
+            (u, v, P), dt, unstable, _ = gpu_run(case.replace(precision=prec), steps, monitor=50)
+            ur, vr, Pr = ora_hist[steps]
+            fin = bool(np.isfinite(ur).all())
+            emit(config="tension_32x32_nh", precision=prec, iterations=steps, mlups=32 * 32 * steps / dt / 1e6,
+                 unstable_gpu=unstable, unstable_oracle=k_nan,
+                 u_err=rel(u, ur) if fin and np.isfinite(u).all() else None,
+                 P_err=rel(P, Pr) if fin and np.isfinite(P).all() else None,
+                 P11_interior=float(P[8:24, 8:24, 0].mean()) if np.isfinite(P).all() else None)
+    # simple shear 256^2, SVK, six Poisson ratios, 20k iterations
+    nsh = args.suite_shear_steps
+    for nu in (0.0, 0.1, 0.2, 0.3, 0.4, 0.45):
+        case = I.shear(256, nsh, model="svk", nu=nu)
+        o = O.OracleSim(case)
+        o.step(nsh)
+        ur, vr, Pr = o.fields()
+        for prec in ("fp64", "fp32", "fp16s"):
+            (u, v, P), dt, unstable, _ = gpu_run(case.replace(precision=prec), nsh, monitor=1000)
+            fin = np.isfinite(ur).all() and np.isfinite(u).all()
+            emit(config="shear_256_svk", nu=nu, precision=prec, iterations=nsh, mlups=256 * 256 * nsh / dt / 1e6,
+                 unstable_gpu=unstable, oracle_finite=bool(np.isfinite(ur).all()),
+                 u_err=rel(u, ur) if fin else None, P_err=rel(P, Pr) if fin else None)
+    # cantilever 4096x256, 100k iterations, tip history every 100 iterations
+    nc = args.suite_cantilever_steps
+    case = I.cantilever(4096, 256, nc)
+    tip = (256 // 2) * 4096 + 4095
+    ref = {}
+    for prec in ("fp64", "fp32", "fp16s"):
+        (u, v, P), dt, unstable, hist = gpu_run(case.replace(precision=prec), nc, monitor=1000, probe=tip,
+                                                every=100)
+        ref[prec] = (u, hist)
+        # the tip history up to its first non-finite sample
+        fin = np.isfinite(hist).all(axis=-1) if len(hist) else np.zeros(0, bool)
+        nfin = int(np.argmin(fin)) if len(fin) and not fin.all() else len(fin)
+        row = dict(config="cantilever_4096x256", precision=prec, iterations=nc, mlups=4096 * 256 * 100 * len(hist) / dt / 1e6,
+                   unstable_gpu=unstable, finite_iterations=100 * nfin,
+                   tip_max=float(np.abs(hist[:nfin]).max()) if nfin else None)
+        if prec != "fp64":
+            h64 = ref["fp64"][1]
+            m = min(nfin, len(h64))
+            while m and not np.isfinite(h64[:m]).all():
+                m -= 1
+            if m:
+                row["tip_history_err_vs_fp64"] = float(np.abs(hist[:m] - h64[:m]).max() / np.abs(h64[:m]).max())
+                row["compared_iterations"] = 100 * m
+            if np.isfinite(u).all() and np.isfinite(ref["fp64"][0]).all():
+                row["u_err_vs_fp64"] = rel(u, ref["fp64"][0])
+        emit(**row)
+    o = O.OracleSim(case.replace(precision="fp64"))
+    o.step(args.suite_cantilever_prefix)
+    with L.Simulation(case.replace(precision="fp64")) as s:
+        s.step(args.suite_cantilever_prefix)
+        s.sync()
+        ug = s.fields()[0]
+    emit(config="cantilever_4096x256", precision="fp64", iterations=args.suite_cantilever_prefix,
+         u_err_vs_oracle=rel(ug, o.fields()[0]))
+    # batched serving
+    emit(config="serving", **serving(L, I, args.serving_requests_suite, args.serving_steps_scale))
+    # roofline 16384^2, 500 iterations
+    case = I.roofline(n=16384, nsteps=500)
+    v0 = I.grf_velocity(case, device=dev)
+    st = torch.cuda.Stream()
+    uref = None
+    for prec in ("fp64", "fp32", "fp16s"):
+        r, u = time_precision(L, I, torch, prec, 16384, 495, 5, st, v0, uref)
+        if prec == "fp64":
+            uref = u
+        emit(config="roofline_16384", precision=prec, **r)
+        del u
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -259,12 +380,21 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-steps-scale", type=float, default=0.1)
+    ap.add_argument("--suite", action="store_true", help="every benchmark configuration, one JSON line each")
+    ap.add_argument("--suite-shear-steps", type=int, default=20000)
+    ap.add_argument("--suite-cantilever-steps", type=int, default=100000)
+    ap.add_argument("--suite-cantilever-prefix", type=int, default=1000)
+    ap.add_argument("--serving-requests-suite", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
 
     from paper_2502_00920_gb300 import replicas as RP
     rank, world, local = RP.ranks()
+    if args.suite:
+        from paper_2502_00920_gb300 import build as B
+        B.build()
+        return suite(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -304,6 +434,7 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = sim.launch_count - launches0
     sim.sync()  # raises if a monitor saw a non-finite value
+    variant = sim.variant
     ms_max = RP.max_over_ranks(ms, world)
     cells = n * n
     value = RP.aggregate_rate(cells * K, ms_max * 1e-3, world) / 1e6
@@ -315,7 +446,9 @@ def main():
     achieved = bpn * cells / (ms / K * 1e-3) / 1e9
     traffic = profile_traffic(args.precision, n)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "step_interior_kernel + step_edge_kernel (one iteration)",
+                "traffic": traffic,
+                "kernel": f"{L.tile_variant_name(args.precision, variant)} + step_edge_kernel (one iteration, "
+                          f"tile variant {variant})",
                 "bytes_per_node": bpn, "peak_source": f"{peak_kind} hbm_gbs"}
     clocks = clk.summary()
     sim.close()

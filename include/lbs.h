@@ -208,6 +208,9 @@ int lbs_set_graph_chunk(lbs_handle *h, int32_t k);
  * default (the fastest on a large lattice); lbs_autotune picks per lattice. */
 int lbs_set_variant(lbs_handle *h, int32_t variant);
 
+/* The handle's current tile variant (LBS_EINVAL for a null handle). */
+int32_t lbs_variant(const lbs_handle *h);
+
 int64_t lbs_iteration(const lbs_handle *h);
 /* first iteration at which a monitor saw a non-finite value, or -1 */
 int64_t lbs_unstable_iteration(const lbs_handle *h);
@@ -241,6 +244,12 @@ int lbs_tile_variants(int32_t precision, int32_t *count, int32_t *tx, int32_t *t
  * (cp.async.bulk.tensor), 0 if it reads global memory directly; negative
  * LBS_EINVAL for an unknown precision or variant. */
 int lbs_tile_variant_kind(int32_t precision, int32_t variant);
+
+/* Name of the kernel that updates a variant's interior tiles (a static
+ * string: "step_interior_kernel", "step_tma_kernel", "step_tma2_kernel" or
+ * "step_march_kernel"; frame tiles always go to "step_edge_kernel"), or NULL
+ * for an unknown precision or variant. */
+const char *lbs_tile_variant_name(int32_t precision, int32_t variant);
 
 /* ---- autotuner ---------------------------------------------------------- */
 

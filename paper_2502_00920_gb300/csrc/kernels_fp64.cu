@@ -22,6 +22,13 @@ TileShape shape(int v) {
   }
 }
 
+const char *name(int v) {
+  switch (v) {
+    case 4: return "step_tma_kernel";
+    default: return "step_interior_kernel";
+  }
+}
+
 cudaError_t step(const Params &p, const StepPtrs &s, int v, cudaStream_t st) {
   switch (v) {
     case 1: return launch_step<V1>(p, s, st);
@@ -51,6 +58,7 @@ const Launchers kL = {kVariants,
                       1 << 4,
                       3,  // default: the fastest on the 16384^2 roofline lattice
                       shape,
+                      name,
                       step,
                       kernels_per_step,
                       tma_maps,

@@ -259,16 +259,16 @@ int check_monitor(lbs_handle *h, bool wait) {
   LBS_CK(q);
   h->mon_pending = false;
   if (h->mon_host[5] != 0.0) {
-    h->unstable_at = h->mon_k;
-    return fail(LBS_EUNSTABLE, "non-finite value at iteration " + std::to_string(h->mon_k));
+    h->unstable_at = (int64_t)h->mon_host[6];
+    return fail(LBS_EUNSTABLE, "non-finite value at iteration " + std::to_string(h->unstable_at));
   }
   return LBS_OK;
 }
 
 int launch_monitor_async(lbs_handle *h) {
   LBS_CK(h->L->monitor(h->P, h->g[h->parity], h->u[h->parity], h->mon_partials, monitor_blocks(h->P), h->mon_out,
-                       h->stream));
-  LBS_CK(cudaMemcpyAsync(h->mon_host, h->mon_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+                       h->k, h->stream));
+  LBS_CK(cudaMemcpyAsync(h->mon_host, h->mon_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LBS_CK(cudaEventRecord(h->mon_event, h->stream));
   h->launches += 2;
   h->mon_pending = true;
@@ -297,7 +297,7 @@ int reset_state_counters(lbs_handle *h) {
   LBS_CK(cudaGetLastError());
   h->launches += 1;
   h->kdev_value = 0;
-  LBS_CK(cudaMemsetAsync(h->mon_out, 0, 6 * sizeof(double), h->stream));
+  LBS_CK(cudaMemsetAsync(h->mon_out, 0, 7 * sizeof(double), h->stream));
   return LBS_OK;
 }
 
@@ -368,6 +368,15 @@ int lbs_tile_variant_kind(int32_t precision, int32_t variant) {
   if (variant < 0 || variant >= L.nvariants) return fail(LBS_EINVAL, "unknown tile variant");
   return (L.tma_mask >> variant) & 1;
 }
+
+const char *lbs_tile_variant_name(int32_t precision, int32_t variant) {
+  if (precision < LBS_FP64 || precision > LBS_FP16S) return nullptr;
+  const Launchers &L = launchers_for(precision);
+  if (variant < 0 || variant >= L.nvariants) return nullptr;
+  return L.name(variant);
+}
+
+int32_t lbs_variant(const lbs_handle *h) { return h ? h->variant : LBS_EINVAL; }
 
 int lbs_tile_variants(int32_t precision, int32_t *count, int32_t *tx, int32_t *ty) {
   if (precision < LBS_FP64 || precision > LBS_FP16S) return fail(LBS_EINVAL, "unknown precision");
@@ -625,7 +634,7 @@ int lbs_monitor(lbs_handle *h, lbs_monitors *out) {
   out->momentum[0] = h->mon_host[2];
   out->momentum[1] = h->mon_host[3];
   out->mass = h->mon_host[4];
-  if (h->mon_host[5] != 0.0 && h->unstable_at < 0) h->unstable_at = h->k;
+  if (h->mon_host[5] != 0.0 && h->unstable_at < 0) h->unstable_at = (int64_t)h->mon_host[6];
   return LBS_OK;
 }
 

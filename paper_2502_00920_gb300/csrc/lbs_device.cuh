@@ -67,6 +67,20 @@ __device__ __forceinline__ void gstore(double *p, size_t i, double v, double) { 
 __device__ __forceinline__ void gstore(float *p, size_t i, float v, float) { p[i] = v; }
 __device__ __forceinline__ void gstore(__half *p, size_t i, float v, float) { p[i] = __float2half_rn(v); }
 
+// FP16 storage holds g in units of g * 2^gshift (an exact power-of-two
+// scaling); the wider types have gshift = 0 and get the factors as
+// compile-time ones.  gscale<gs, R>(P) = 2^gshift, gscale_inv = 2^-gshift.
+template <class G, class R>
+__host__ __device__ __forceinline__ R gscale(const Params &P) {
+  if constexpr (sizeof(G) == 2) return (R)ldexp(1.0, P.gshift);
+  else return R(1);
+}
+template <class G, class R>
+__host__ __device__ __forceinline__ R gscale_inv(const Params &P) {
+  if constexpr (sizeof(G) == 2) return (R)ldexp(1.0, -P.gshift);
+  else return R(1);
+}
+
 // difference of two displacement records, as the compute type
 __device__ __forceinline__ void udiff(const double2 &a, const double2 &b, double &dx, double &dy) {
   dx = a.x - b.x;
@@ -529,7 +543,7 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
   const R *bnd = (const R *)S.b_in;
   const int64_t k = EDGE ? (*S.kptr + S.koff) : 0;
   // g is held in units of g * 2^gshift (1 unless FP16 storage)
-  const R inv = (R)ldexp(1.0, -P.gshift), scl = (R)ldexp(1.0, P.gshift);
+  const R inv = gscale_inv<typename C::gs, R>(P), scl = gscale<typename C::gs, R>(P);
   const R kap = (R)P.kappa * inv;
   const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
 
@@ -825,7 +839,7 @@ __global__ void __launch_bounds__(C::NT) step_tma_kernel(const Params P, const S
   }
 
   // g is held in units of g * 2^gshift (1 unless FP16 storage)
-  const R inv = (R)ldexp(1.0, -P.gshift), scl = (R)ldexp(1.0, P.gshift);
+  const R inv = gscale_inv<typename C::gs, R>(P), scl = gscale<typename C::gs, R>(P);
   const R kap = (R)P.kappa * inv;
   auto G = [&](int q, int r, int c) -> R {
     const gs v = sg[((size_t)q * T::GH + r) * T::GW + c];
@@ -966,7 +980,7 @@ __global__ void __launch_bounds__(C::NT) step_tma2_kernel(const Params P, const 
     }
   }
   __syncthreads();
-  const R inv = (R)ldexp(1.0, -P.gshift), scl = (R)ldexp(1.0, P.gshift);
+  const R inv = gscale_inv<typename C::gs, R>(P), scl = gscale<typename C::gs, R>(P);
   const R kap = (R)P.kappa * inv;
   const size_t plane = (size_t)P.ny * P.pitch;
   const R omega = (R)P.omega, sigma = (R)P.sigma, hdx = R(0.5) * (R)P.inv_dx;
@@ -1096,6 +1110,252 @@ cudaError_t launch_step_tma2(const Params &P, const StepPtrs &S, cudaStream_t st
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ row-marching strips
+// A block owns one TX-wide column of interior tiles over a segment of SH rows
+// and marches up it RB rows at a time, one thread per output node of a step.
+// Ring buffers in shared memory hold the g rows (nine planes each), u rows and
+// N rows still needed; each step loads only its RB new g rows and RB new u
+// rows (one TMA row copy each, issued D steps ahead), so the halo is
+// recomputed only across x.  Step j (output rows [y, y+RB)): u(t+dt) for rows
+// [y+2, y+RB+2), N for rows [y+1, y+RB+1), then streaming, source, collision
+// and stores for rows [y, y+RB).
+template <class C, int RB_, int SH_, int D_>
+struct MarchCfg {
+  using T = TmaCfg<C>;
+  using gs = typename C::gs;
+  using us = typename C::us;
+  using real = typename C::real;
+  static constexpr int TX = C::TX, RB = RB_, SH = SH_, D = D_, NT = RB * TX;
+  static constexpr int GW = T::GW, XO = T::XO, UW = T::UW, W1 = TX + 2, UEL = T::UEL;
+  static constexpr int CG = 32, CU = 32, CN = 16;  // ring sizes (rows), powers of two
+  // rows in use at step j plus the rows of the D steps in flight
+  static_assert(CG >= (D + 1) * RB + 4 && CU >= (D + 1) * RB + 2 && CN >= RB + 2, "rings too small");
+  static_assert(SH % RB == 0 && C::TY % RB == 0, "segments split into whole steps");
+  static_assert(NT <= 1024 && NT % 32 == 0, "one thread per output node of a step");
+  static constexpr size_t G_ROW = (size_t)9 * GW * sizeof(gs);  // bytes one row copy delivers
+  static constexpr size_t U_ROW = (size_t)UW * sizeof(us);
+  // ring slots start on 128-byte boundaries (the shared-memory alignment of a
+  // tensor copy's destination)
+  static constexpr size_t G_SLOT = (G_ROW + 127) / 128 * 128;
+  static constexpr size_t U_SLOT = (U_ROW + 127) / 128 * 128;
+  static_assert(G_SLOT % sizeof(gs) == 0 && U_SLOT % sizeof(us) == 0, "slot strides in elements");
+  static constexpr size_t OFF_U = (size_t)CG * G_SLOT;
+  static constexpr size_t OFF_N = OFF_U + (size_t)CU * U_SLOT;
+  static constexpr size_t OFF_BAR = OFF_N + ((size_t)CN * 4 * W1 * sizeof(real) + 15) / 16 * 16;
+  static constexpr size_t SMEM = OFF_BAR + 8 * (D + 1);  // bar[0..D-1]: steps, bar[D]: prologue
+};
+
+template <class M>
+__device__ __forceinline__ void march_issue(unsigned char *dsm, uint64_t *bar, const CUtensorMap &tm_g,
+                                            const CUtensorMap &tm_u, int x0, int g_lo, int ng, int gbase, int u_lo,
+                                            int nu, int ubase) {
+  mbar_expect_tx(bar, (uint32_t)(ng * M::G_ROW + nu * M::U_ROW));
+  for (int r = g_lo; r < g_lo + ng; ++r)
+    tma_load_3d(dsm + (size_t)((r - gbase) & (M::CG - 1)) * M::G_SLOT, &tm_g, x0 - M::XO, r, 0, bar);
+  for (int r = u_lo; r < u_lo + nu; ++r)
+    tma_load_2d(dsm + M::OFF_U + (size_t)((r - ubase) & (M::CU - 1)) * M::U_SLOT, &tm_u, M::UEL * (x0 - 2), r, bar);
+}
+
+__device__ __forceinline__ bool march_wait(uint64_t *bar, uint32_t parity) {
+  int ok = 0;
+  for (uint32_t it = 0; it < kMaxPolls; ++it)
+    if (mbar_try_wait(bar, parity)) {
+      ok = 1;
+      break;
+    }
+  return __syncthreads_and(ok) != 0;
+}
+
+template <class C, class M>
+__global__ void __launch_bounds__(M::NT) step_march_kernel(const Params P, const StepPtrs S,
+                                                           const __grid_constant__ CUtensorMap tm_g,
+                                                           const __grid_constant__ CUtensorMap tm_u, int a_lo, int ni,
+                                                           int y_first, int y_last) {
+  using R = typename C::real;
+  using us = typename C::us;
+  using gs = typename C::gs;
+  constexpr int RB = M::RB, D = M::D, NT = M::NT, CG = M::CG, CU = M::CU, CN = M::CN, GW = M::GW, UW = M::UW,
+                W1 = M::W1;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  const gs *gr = (const gs *)dsm;             // [CG] slots of [9][GW]
+  us *ur = (us *)(dsm + M::OFF_U);            // [CU] slots of [UW]
+  R *nr = (R *)(dsm + M::OFF_N);              // [CN][4][W1]
+  uint64_t *bar = (uint64_t *)(dsm + M::OFF_BAR);
+  const int x0 = (a_lo + (int)(blockIdx.x % ni)) * C::TX;
+  const int ys = y_first + (int)(blockIdx.x / ni) * M::SH;
+  const int ye = min(ys + M::SH, y_last);
+  const int nsteps = (ye - ys) / RB;
+  const int gbase = ys - 3, ubase = ys - 2, nbase = ys - 1;
+  auto G = [&](int q, int row, int c) -> R {
+    const gs v = gr[(size_t)((row - gbase) & (CG - 1)) * (M::G_SLOT / sizeof(gs)) + q * GW + c];
+    if constexpr (sizeof(gs) == 2) return __half2float(v);
+    else return (R)v;
+  };
+  auto U = [&](int row, int cx) -> us & { return ur[(size_t)((row - ubase) & (CU - 1)) * (M::U_SLOT / sizeof(us)) + cx]; };
+  auto N = [&](int m, int row, int rx) -> R & { return nr[((size_t)((row - nbase) & (CN - 1)) * 4 + m) * W1 + rx]; };
+  // the rows step j needs that no earlier copy brought: g [y+3, y+RB+3), u [y+2, y+RB+2)
+  auto issue_step = [&](int j) {
+    const int y = ys + j * RB;
+    march_issue<M>(dsm, &bar[j % D], tm_g, tm_u, x0, y + 3, RB, gbase, y + 2, RB, ubase);
+  };
+
+  const R inv = gscale_inv<gs, R>(P), scl = gscale<gs, R>(P);
+  const R kap = (R)P.kappa * inv, hdx = R(0.5) * (R)P.inv_dx;
+  const R lam = (R)P.lam, mu = (R)P.mu, omega = (R)P.omega, sigma = (R)P.sigma;
+  const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
+  const size_t plane = (size_t)P.ny * P.pitch;
+  gs *__restrict__ go = (gs *)S.g_out;
+  us *__restrict__ uo = (us *)S.u_out;
+
+  // u(t+dt) in place for rows [r0, r0 + nrow) (x: x0-2 .. x0+TX+1)
+  auto phase_u = [&](int r0, int nrow) {
+    for (int e = threadIdx.x; e < nrow * UW; e += NT) {
+      const int row = r0 + e / UW, cx = e % UW, gc = cx + M::XO - 2;
+      R p[9], o[9];
+#pragma unroll
+      for (int q = 1; q < 9; ++q) {
+        p[q] = G(q, row - ey(q), gc - ex(q));
+        o[q] = G(q, row, gc);
+      }
+      const R gx = (o[1] - o[3]) + (o[5] - o[6]) + (o[8] - o[7]);
+      const R gy = (o[2] - o[4]) + (o[5] - o[8]) + (o[6] - o[7]);
+      const R fx = (p[1] - p[3]) + (p[5] - p[6]) + (p[8] - p[7]);
+      const R fy = (p[2] - p[4]) + (p[5] - p[8]) + (p[6] - p[7]);
+      us &uu = U(row, cx);
+      uu = uadd(uu, kap * (gx + fx), kap * (gy + fy));
+    }
+  };
+  // N for rows [r0, r0 + nrow) (x: x0-1 .. x0+TX)
+  auto phase_n2 = [&](int r0, int nrow) {
+    for (int e = threadIdx.x; e < nrow * W1; e += NT) {
+      const int row = r0 + e / W1, rx = e % W1, cx = rx + 1;
+      R dxx, dxy, dyx, dyy, H[4], Nn[4];
+      udiff(U(row, cx + 1), U(row, cx - 1), dxx, dxy);
+      udiff(U(row + 1, cx), U(row - 1, cx), dyx, dyy);
+      H[0] = dxx * hdx;
+      H[1] = dyx * hdx;
+      H[2] = dxy * hdx;
+      H[3] = dyy * hdx;
+      material<R>(P, lam, mu, H, Nn);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) N(m, row, rx) = Nn[m];
+    }
+  };
+
+  // prologue: the warm-up rows (bar[D]) and the first D steps' rows
+  if (threadIdx.x == 0) {
+    for (int b = 0; b <= D; ++b) mbar_init(&bar[b], 1);
+    march_issue<M>(dsm, &bar[D], tm_g, tm_u, x0, ys - 3, 6, gbase, ys - 2, 4, ubase);
+    for (int j = 0; j < D && j < nsteps; ++j) issue_step(j);
+  }
+  __syncthreads();
+  if (!march_wait(&bar[D], 0)) {
+    // let the copies in flight land before the block leaves
+    if (threadIdx.x == 0) {
+      if (S.err) atomicExch(S.err, 1);
+      for (int j = 0; j < D && j < nsteps; ++j)
+        for (uint32_t it = 0; it < kMaxPolls; ++it)
+          if (mbar_try_wait(&bar[j], 0)) break;
+    }
+    return;
+  }
+  phase_u(ys - 2, 4);
+  __syncthreads();
+  phase_n2(ys - 1, 2);
+  // (the barrier at the top of the first step orders these before their use)
+
+  const int lx = threadIdx.x % C::TX, ly = threadIdx.x / C::TX, rx = lx + 1, gc = lx + M::XO;
+  for (int j = 0; j < nsteps; ++j) {
+    const int y = ys + j * RB;
+    // this step's rows arrived?  (bar[j % D] completes once per D steps)
+    if (!march_wait(&bar[j % D], (uint32_t)((j / D) & 1))) {
+      if (threadIdx.x == 0) {
+        if (S.err) atomicExch(S.err, 1);
+        for (int i = j + 1; i < j + D && i < nsteps; ++i)
+          for (uint32_t it = 0; it < kMaxPolls; ++it)
+            if (mbar_try_wait(&bar[i % D], (uint32_t)((i / D) & 1))) break;
+      }
+      return;
+    }
+    // prefetch step j + D into slots of rows no longer needed (the reads of
+    // those slots ended before the barrier that closed step j - 1)
+    if (threadIdx.x == 0 && j + D < nsteps) {
+      fence_async_shared();
+      issue_step(j + D);
+    }
+    phase_u(y + 2, RB);
+    __syncthreads();
+    phase_n2(y + 1, RB);
+    __syncthreads();
+    // output node (x0 + lx, y + ly)
+    {
+      const int row = y + ly;
+      R f[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) f[q] = G(q, row - ey(q), gc - ex(q));
+      const R Sx = (N(0, row, rx + 1) - N(0, row, rx - 1)) * hdx + (N(1, row + 1, rx) - N(1, row - 1, rx)) * hdx + sbx;
+      const R Sy = (N(2, row, rx + 1) - N(2, row, rx - 1)) * hdx + (N(3, row + 1, rx) - N(3, row - 1, rx)) * hdx + sby;
+      collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
+      const size_t idx = (size_t)row * P.pitch + (x0 + lx);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[q], scl);
+      uo[idx] = U(row, lx + 2);
+    }
+    __syncthreads();
+  }
+}
+
+template <class C, class M>
+cudaError_t launch_step_march(const Params &P, const StepPtrs &S, cudaStream_t st) {
+  const int ntx = (P.nx + C::TX - 1) / C::TX, nty = (P.ny + C::TY - 1) / C::TY;
+  int a_lo, a_hi, b_lo, b_hi;
+  interior_range(P.nx, P.ny, C::TX, C::TY, a_lo, a_hi, b_lo, b_hi);
+  const int ni = a_hi - a_lo, nj = b_hi - b_lo;
+  if (ni > 0 && nj > 0) {
+    if (!S.tm_g || !S.tm_u) return cudaErrorInvalidValue;
+    const int y_first = b_lo * C::TY, y_last = b_hi * C::TY;
+    const int nseg = (y_last - y_first + M::SH - 1) / M::SH;
+    step_march_kernel<C, M><<<ni * nseg, M::NT, M::SMEM, st>>>(P, S, *(const CUtensorMap *)S.tm_g,
+                                                               *(const CUtensorMap *)S.tm_u, a_lo, ni, y_first, y_last);
+  }
+  const int nedge = ntx * nty - ni * nj;
+  if (nedge > 0) step_edge_kernel<C><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+  return cudaGetLastError();
+}
+
+// row-box TMA descriptors (one g row with its nine planes; one u row)
+template <class C, class M>
+bool make_march_maps(const Params &P, const void *g, const void *u, void *out_g, void *out_u) {
+  using gs = typename C::gs;
+  using R = typename C::real;
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  auto encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  const CUtensorMapDataType gt = sizeof(gs) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : sizeof(gs) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const cuuint64_t gdim[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.ny, 9};
+  const cuuint64_t gstr[2] = {(cuuint64_t)P.pitch * sizeof(gs), (cuuint64_t)P.ny * P.pitch * sizeof(gs)};
+  const cuuint32_t gbox[3] = {(cuuint32_t)M::GW, 1, 9};
+  const cuuint32_t est[3] = {1, 1, 1};
+  CUresult r1 = encode((CUtensorMap *)out_g, gt, 3, const_cast<void *>(g), gdim, gstr, gbox, est,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUtensorMapDataType ut = sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t udim[2] = {(cuuint64_t)M::UEL * P.pitch, (cuuint64_t)P.ny};
+  const cuuint64_t ustr[1] = {(cuuint64_t)M::UEL * P.pitch * sizeof(R)};
+  const cuuint32_t ubox[2] = {(cuuint32_t)(M::UEL * M::UW), 1};
+  CUresult r2 = encode((CUtensorMap *)out_u, ut, 2, const_cast<void *>(u), udim, ustr, ubox, est,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return false;
+  return cudaFuncSetAttribute(step_march_kernel<C, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::SMEM) ==
+         cudaSuccess;
+}
+
 // TMA descriptors for one (g, u) buffer pair and the kernel's shared-memory
 // opt-in (host side; called when a handle selects a TMA tile variant)
 template <class C>
@@ -1172,7 +1432,7 @@ __global__ void __launch_bounds__(C::NT) init_kernel(const Params P, typename C:
   phase_n<C, true>(sm, P, x0, y0, bnd);
   __syncthreads();
   const size_t plane = (size_t)P.ny * P.pitch;
-  const R idx_ = (R)P.inv_dx, scl = (R)ldexp(1.0, P.gshift);
+  const R idx_ = (R)P.inv_dx, scl = gscale<typename C::gs, R>(P);
   const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
   for (int i = 0; i < C::CPT; ++i) {
     const int lx = tx, ly = ty + i * C::NTY, x = x0 + lx, y = y0 + ly;
@@ -1218,7 +1478,7 @@ __global__ void __launch_bounds__(C::NT) fields_kernel(const Params P, const typ
   phase_n<C, true>(sm, P, x0, y0, (R *)nullptr);
   __syncthreads();
   const size_t plane = (size_t)P.ny * P.pitch;
-  const R idx_ = (R)P.inv_dx, inv = (R)ldexp(1.0, -P.gshift), mu = (R)P.mu;
+  const R idx_ = (R)P.inv_dx, inv = gscale_inv<typename C::gs, R>(P), mu = (R)P.mu;
   const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
   for (int i = 0; i < C::CPT; ++i) {
     const int lx = tx, ly = ty + i * C::NTY, x = x0 + lx, y = y0 + ly;
@@ -1276,7 +1536,7 @@ __global__ void __launch_bounds__(kMonThreads) monitor_kernel(const Params P, co
                                                               const typename C::us *u, double *partials) {
   using R = typename C::real;
   const size_t n = (size_t)P.nx * P.ny, plane = (size_t)P.ny * P.pitch;
-  const R inv = (R)ldexp(1.0, -P.gshift);
+  const R inv = gscale_inv<typename C::gs, R>(P);
   double bad = 0, umax = 0, mx = 0, my = 0, mass = 0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % P.nx), y = (int)(i / P.nx);
@@ -1325,8 +1585,9 @@ __global__ void __launch_bounds__(kMonThreads) monitor_kernel(const Params P, co
 }
 
 // final pass over nblocks partials; out[0..4] = bad, max|u|, momentum x, y, mass;
-// out[5] = 1 if anything was non-finite (a sticky flag: never cleared here)
-static __global__ void monitor_final_kernel(const double *partials, int nblocks, double *out) {
+// out[5] = 1 if anything was non-finite (a sticky flag: never cleared here);
+// out[6] = the iteration of the first monitor that set it
+static __global__ void monitor_final_kernel(const double *partials, int nblocks, double *out, double k) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double o[5] = {0, 0, 0, 0, 0};
   for (int b = 0; b < nblocks; ++b) {
@@ -1337,7 +1598,10 @@ static __global__ void monitor_final_kernel(const double *partials, int nblocks,
     o[4] += partials[(size_t)b * 5 + 4];
   }
   for (int m = 0; m < 5; ++m) out[m] = o[m];
-  if (o[0] > 0 || !isfinite(o[1])) out[5] = 1.0;
+  if ((o[0] > 0 || !isfinite(o[1])) && out[5] == 0.0) {
+    out[5] = 1.0;
+    out[6] = k;
+  }
 }
 
 template <class C>
@@ -1369,9 +1633,9 @@ cudaError_t launch_fields(const Params &P, const void *g, const void *u, double 
 
 template <class C>
 cudaError_t launch_monitor(const Params &P, const void *g, const void *u, double *partials, int nblocks, double *out6,
-                           cudaStream_t st) {
+                           int64_t k, cudaStream_t st) {
   monitor_kernel<C><<<nblocks, kMonThreads, 0, st>>>(P, (const typename C::gs *)g, (const typename C::us *)u, partials);
-  monitor_final_kernel<<<1, 32, 0, st>>>(partials, nblocks, out6);
+  monitor_final_kernel<<<1, 32, 0, st>>>(partials, nblocks, out6, (double)k);
   return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(C::NT) fields_rows_kernel(const Params P, cons
   phase_n<C, true>(sm, P, x0, y0, (R *)nullptr);
   __syncthreads();
   const size_t plane = (size_t)P.ny * P.pitch;
-  const R idx_ = (R)P.inv_dx, inv = (R)ldexp(1.0, -P.gshift), mu = (R)P.mu;
+  const R idx_ = (R)P.inv_dx, inv = gscale_inv<typename C::gs, R>(P), mu = (R)P.mu;
   const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
   for (int i = 0; i < C::CPT; ++i) {
     const int lx = tx, ly = ty + i * C::NTY, x = x0 + lx, y = y0 + ly;

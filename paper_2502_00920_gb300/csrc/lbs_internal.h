@@ -75,6 +75,7 @@ struct Launchers {
   int tma_mask;   // bit v set: variant v stages its interior tiles by TMA
   int default_variant;
   TileShape (*shape)(int variant);
+  const char *(*name)(int variant);  // the interior kernel of a variant, e.g. "step_tma_kernel"
   cudaError_t (*step)(const Params &p, const StepPtrs &s, int variant, cudaStream_t st);
   int (*kernels_per_step)(const Params &p, int variant);
   // TMA descriptors of one (g, u) buffer pair for a tile variant; returns
@@ -85,7 +86,7 @@ struct Launchers {
   cudaError_t (*fields)(const Params &p, const void *g, const void *u, double *uo, double *vo, double *Po,
                         cudaStream_t st);
   cudaError_t (*monitor)(const Params &p, const void *g, const void *u, double *partials, int nblocks,
-                         double *out6, cudaStream_t st);
+                         double *out7, int64_t k, cudaStream_t st);
   cudaError_t (*probe)(const Params &p, const void *u, const int32_t *idx, int n, double *out, cudaStream_t st);
   // one iteration of every unfinished lattice of a batch: interior tiles,
   // frame tiles, then the per-lattice counters (tile shape of the default

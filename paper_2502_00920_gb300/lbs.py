@@ -93,6 +93,8 @@ SIGNATURES = {
     "lbs_constitutive": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]),
     "lbs_tile_variants": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, _i32p]),
     "lbs_tile_variant_kind": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
+    "lbs_tile_variant_name": (ctypes.c_char_p, [ctypes.c_int32, ctypes.c_int32]),
+    "lbs_variant": (ctypes.c_int32, [_vp]),
     "lbs_set_allocator": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbs_autotune": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(Material), ctypes.POINTER(Bcs),
                                     ctypes.c_int32, _i32p, ctypes.POINTER(ctypes.c_float)]),
@@ -230,6 +232,14 @@ def tile_variant_kind(precision: str, variant: int) -> str:
     return "tma" if k == 1 else "global"
 
 
+def tile_variant_name(precision: str, variant: int) -> str:
+    """Name of the kernel that updates the variant's interior tiles."""
+    n = lib().lbs_tile_variant_name(PRECISION[precision], int(variant))
+    if n is None:
+        raise LbsError(EINVAL, f"unknown tile variant {variant} for {precision}")
+    return n.decode()
+
+
 def _dev_ptr(t):
     if t is None:
         return None
@@ -317,6 +327,10 @@ class Simulation:
 
     def set_variant(self, v: int):
         check(lib().lbs_set_variant(self._h, int(v)))
+
+    @property
+    def variant(self) -> int:
+        return int(lib().lbs_variant(self._h))
 
     # -- outputs
     def fields(self, u=True, v=True, P=True):
