@@ -183,24 +183,30 @@ def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: floa
     fetch fields, destroy) and records its service time; its FIFO queue under
     the arrival times is then exact: done_i = max(arrival_i, done_{i-1}) +
     service_i.  Arrivals are Poisson at `load` times that baseline's capacity.
-    The FP32 server then receives the same arrivals in real time."""
+    The FP32 server then receives the same arrivals in real time (latency
+    p50/p99), and, on a fresh server, the whole trace at once (capacity:
+    node updates / makespan, against the baseline's node updates / total
+    service time).  A request has failed if the library reported it unstable
+    or its final u holds a non-finite value.  Every request finite in both
+    arms states its FP32 error on u against its FP64 result."""
     import threading
     trace = I.serving_trace(n_requests, seed=seed, rate=1.0)
     cases = [c.replace(nsteps=max(100, int(round(c.nsteps * steps_scale)))) for _, c in trace]
     work = [c.nx * c.ny * c.nsteps for c in cases]
     # one at a time, FP64
-    service = []
-    failed_seq = 0
+    service, u64 = [], []
     for c in cases:
         t0 = time.perf_counter()
+        u = None
         try:
             with L.Simulation(c.replace(precision="fp64")) as s:
                 s.step(c.nsteps)
                 s.sync()
-                s.fields(True, True, True)
+                u, _, _ = s.fields(True, True, True)
         except L.LbsError:
-            failed_seq += 1
+            pass
         service.append(time.perf_counter() - t0)
+        u64.append(u if u is not None and np.isfinite(u).all() else None)
     capacity = len(cases) / sum(service)
     rate = load * capacity
     gaps = [a for a, _ in trace]
@@ -210,38 +216,63 @@ def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: floa
         t = max(a, t) + sv
         done.append(t)
     seq_ttr = [d - a for d, a in zip(done, arrivals)]
-    seq_mlups = sum(work) / (done[-1] - arrivals[0]) / 1e6
-    # batched, FP32
-    srv = L.Server(precision="fp32", chunk=64)
-    tickets = [None] * len(cases)
-    t_start = time.perf_counter()
+    q = lambda xs, p: sorted(xs)[min(len(xs) - 1, int(round(p * (len(xs) - 1))))]
 
-    def submitter():
-        for i, (a, c) in enumerate(zip(arrivals, cases)):
-            delay = a - (time.perf_counter() - t_start)
-            if delay > 0:
-                time.sleep(delay)
-            tickets[i] = srv.submit(c.replace(precision="fp32"))
+    def collect(srv, tickets):
+        infos = [srv.poll(tk) for tk in tickets]
+        us = []
+        for tk in tickets:
+            u, _, _, rc = srv.result(tk)
+            us.append(u if rc == L.OK and np.isfinite(u).all() else None)
+        return infos, us
 
-    th = threading.Thread(target=submitter)
-    th.start()
-    th.join()
-    srv.drain(-1)
-    infos = [srv.poll(tk) for tk in tickets]
-    stats = srv.stats()
-    for tk in tickets:
-        srv.result(tk)
-    srv.close()
+    # batched FP32, Poisson arrivals in real time
+    with L.Server(precision="fp32", chunk=64) as srv:
+        tickets = [None] * len(cases)
+        t_start = time.perf_counter()
+
+        def submitter():
+            for i, (a, c) in enumerate(zip(arrivals, cases)):
+                delay = a - (time.perf_counter() - t_start)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[i] = srv.submit(c.replace(precision="fp32"))
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        srv.drain(-1)
+        stats = srv.stats()
+        infos, u32 = collect(srv, tickets)
     ttr = [i["t_done"] - i["t_submit"] for i in infos]
     span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
-    q = lambda xs, p: sorted(xs)[min(len(xs) - 1, int(round(p * (len(xs) - 1))))]
-    return {"requests": len(cases), "steps_scale": steps_scale, "offered_load_x_fp64_capacity": load,
-            "arrival_rate_per_s": rate, "node_updates": sum(work),
-            "batched_fp32": {"aggregate_mlups": sum(work) / span / 1e6, "p50_s": q(ttr, 0.5), "p99_s": q(ttr, 0.99),
-                             "failed": int(sum(i["state"] == "failed" for i in infos)),
-                             "launches": stats["launches"], "busy_s": stats["busy_seconds"]},
-            "sequential_fp64": {"aggregate_mlups": seq_mlups, "p50_s": q(seq_ttr, 0.5), "p99_s": q(seq_ttr, 0.99),
-                                "failed": failed_seq, "service_s": sum(service)}}
+    # batched FP32, the whole trace at once
+    with L.Server(precision="fp32", chunk=64) as srv:
+        t0 = time.perf_counter()
+        tickets = [srv.submit(c.replace(precision="fp32")) for c in cases]
+        srv.drain(-1)
+        makespan = time.perf_counter() - t0
+        sat_infos, sat_u = collect(srv, tickets)
+    errs = [float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+            for a, b in zip(u32, u64) if a is not None and b is not None]
+    return {"requests": len(cases), "steps_scale": steps_scale, "node_updates": sum(work),
+            "offered_load_x_fp64_capacity": load, "arrival_rate_per_s": rate,
+            "sequential_fp64": {"aggregate_mlups": sum(work) / sum(service) / 1e6,
+                                "p50_s": q(seq_ttr, 0.5), "p99_s": q(seq_ttr, 0.99),
+                                "failed": sum(u is None for u in u64), "service_s": sum(service)},
+            "batched_fp32_poisson": {"aggregate_mlups": sum(work) / span / 1e6, "p50_s": q(ttr, 0.5),
+                                     "p99_s": q(ttr, 0.99), "failed": sum(u is None for u in u32),
+                                     "launches": stats["launches"], "busy_s": stats["busy_seconds"]},
+            "batched_fp32_saturated": {"aggregate_mlups": sum(work) / makespan / 1e6, "makespan_s": makespan,
+                                       "failed": sum(u is None for u in sat_u),
+                                       "equal_to_poisson_run": all(
+                                           (a is None and b is None) or (a is not None and b is not None
+                                                                          and np.array_equal(a, b))
+                                           for a, b in zip(u32, sat_u))},
+            "failed_fp32_only": sum(a is None and b is not None for a, b in zip(u32, u64)),
+            "failed_fp64_only": sum(a is not None and b is None for a, b in zip(u32, u64)),
+            "u_err_fp32_vs_fp64": {"compared": len(errs), "max": max(errs) if errs else None,
+                                   "median": float(np.median(errs)) if errs else None}}
 
 
 def suite(args):
@@ -348,7 +379,7 @@ def suite(args):
     emit(config="cantilever_4096x256", precision="fp64", iterations=args.suite_cantilever_prefix,
          u_err_vs_oracle=rel(ug, o.fields()[0]))
     # batched serving
-    emit(config="serving", **serving(L, I, args.serving_requests_suite, args.serving_steps_scale))
+    emit(config="serving", **serving(L, I, args.serving_requests_suite, args.suite_serving_steps_scale))
     # roofline 16384^2, 500 iterations
     case = I.roofline(n=16384, nsteps=500)
     v0 = I.grf_velocity(case, device=dev)
@@ -385,6 +416,7 @@ def main():
     ap.add_argument("--suite-cantilever-steps", type=int, default=100000)
     ap.add_argument("--suite-cantilever-prefix", type=int, default=1000)
     ap.add_argument("--serving-requests-suite", type=int, default=512)
+    ap.add_argument("--suite-serving-steps-scale", type=float, default=1.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
