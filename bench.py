@@ -272,7 +272,8 @@ def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: floa
             "failed_fp32_only": sum(a is None and b is not None for a, b in zip(u32, u64)),
             "failed_fp64_only": sum(a is not None and b is None for a, b in zip(u32, u64)),
             "u_err_fp32_vs_fp64": {"compared": len(errs), "max": max(errs) if errs else None,
-                                   "median": float(np.median(errs)) if errs else None}}
+                                   "median": float(np.median(errs)) if errs else None,
+                                   "above_1e-5": sum(e > 1e-5 for e in errs)}}
 
 
 def suite(args):

@@ -78,7 +78,7 @@ bool tma_maps(const Params &p, int v, const void *g, const void *u, void *og, vo
 
 const Launchers kL = {kVariants,
                       (1 << 4) | (1 << 5) | (1 << 6) | (1 << 7),
-                      7,  // default: the fastest on the 16384^2 roofline lattice
+                      4,  // default: the fastest on the 16384^2 roofline lattice
                       shape,
                       name,
                       step,

@@ -300,47 +300,45 @@ __device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t 
 }
 
 // ------------------------------------------------------------------ collision
-// BGK collision with forcing (Alg. 1): g = f - (f - feq)/tau + (1 - 1/(2 tau)) psi dt
-// in reduced variables: jj = c j / cs^2 = 3 sum e f + (sigma/2) S,
-// A = Pi / cs^2 = 3 sum e e f, sigma = c dt / cs^2,
-// feq_q = w_q (r (2 - 3|e|^2/2) + e.jj + 3/2 e.A.e - trA/2),
-// (1 - 1/(2 tau)) psi_q dt = w_q e.F, F = (1 - omega/2) sigma S.
+// BGK collision with forcing (Alg. 1): g = f - (f - feq)/tau + (1 - 1/(2 tau)) psi dt.
+// feq (Eq. feq, second-order Hermite) takes r, j = c sum e f + dt/2 S and
+// Pi = sum c c f from f itself, so f - feq has no component along r, j or Pi:
+// written out in the populations it is, with the pair sums and differences
+//   s13 = f1 + f3, d13 = f1 - f3 (likewise 24, 57, 68),
+// one even combination Q = f0 - 2 (s13 + s24) + 4 (s57 + s68), giving
+//   (f - feq)_q even part = w_q Q chi_q,  chi = 1/4 (rest), -1/2 (axes), 1 (diagonals),
+// and four odd ones (the odd parts of f - feq on the axis and diagonal pairs)
+//   ox = d13/6 - (d57 - d68)/3,   oy = d24/6 - (d57 + d68)/3,
+//   o57 = d57/3 - (d13 + d24)/12, o68 = d68/3 - (d24 - d13)/12,
+// each less the dt/2 S part of j, which combines with the forcing term
+// (1 - 1/(2 tau)) psi dt into w_q sigma e_q.S per population (sigma = c dt / cs^2;
+// its first moment is sigma S / 3 = dt S / c, the momentum the source adds).
+// So g_q = f_q - omega (f - feq)_q + w_q sigma e_q.S.  The same algebra as
+// the literal moment form, but every intermediate is of the size of the
+// populations, so single-precision rounding stays at the level of the stored
+// values instead of that of the second moments.
 template <class R>
 __device__ __forceinline__ void collide(R f[9], R Sx, R Sy, R omega, R sigma) {
-  // opposite pairs (1,3), (2,4), (5,7), (6,8): even and odd parts
   const R s13 = f[1] + f[3], s24 = f[2] + f[4], s57 = f[5] + f[7], s68 = f[6] + f[8];
   const R d13 = f[1] - f[3], d24 = f[2] - f[4], d57 = f[5] - f[7], d68 = f[6] - f[8];
-  const R r = f[0] + (s13 + s24) + (s57 + s68);
-  const R m1x = d13 + (d57 - d68);
-  const R m1y = d24 + (d57 + d68);
-  const R Axx = R(3) * (s13 + (s57 + s68));
-  const R Ayy = R(3) * (s24 + (s57 + s68));
-  const R Axy = R(3) * (s57 - s68);
-  const R trA = Axx + Ayy;
-  const R jx = R(3) * m1x + R(0.5) * sigma * Sx;
-  const R jy = R(3) * m1y + R(0.5) * sigma * Sy;
-  const R fs = (R(1) - R(0.5) * omega) * sigma;
-  const R Fx = fs * Sx, Fy = fs * Sy;
-  const R w0 = wq<R>(0), w1 = wq<R>(1), w5 = wq<R>(5);
-  // even (E) and odd (J) parts of feq per pair, and the forcing term (Fq)
-  const R E0 = w0 * (R(2) * r - R(0.5) * trA);
-  const R Ex = w1 * (R(0.5) * r + R(1.5) * Axx - R(0.5) * trA);
-  const R Ey = w1 * (R(0.5) * r + R(1.5) * Ayy - R(0.5) * trA);
-  const R E57 = w5 * (trA - r + R(3) * Axy);
-  const R E68 = w5 * (trA - r - R(3) * Axy);
-  const R Jx = w1 * jx, Jy = w1 * jy, J57 = w5 * (jx + jy), J68 = w5 * (jy - jx);
-  const R Fqx = w1 * Fx, Fqy = w1 * Fy, F57 = w5 * (Fx + Fy), F68 = w5 * (Fy - Fx);
-  // g = f - omega (f - feq) + forcing: the non-equilibrium part f - feq is
-  // small, so this form keeps the rounding error relative to it
-  f[0] = f[0] - omega * (f[0] - E0);
-  f[1] = f[1] - omega * (f[1] - (Ex + Jx)) + Fqx;
-  f[3] = f[3] - omega * (f[3] - (Ex - Jx)) - Fqx;
-  f[2] = f[2] - omega * (f[2] - (Ey + Jy)) + Fqy;
-  f[4] = f[4] - omega * (f[4] - (Ey - Jy)) - Fqy;
-  f[5] = f[5] - omega * (f[5] - (E57 + J57)) + F57;
-  f[7] = f[7] - omega * (f[7] - (E57 - J57)) - F57;
-  f[6] = f[6] - omega * (f[6] - (E68 + J68)) + F68;
-  f[8] = f[8] - omega * (f[8] - (E68 - J68)) - F68;
+  const R Q = f[0] - R(2) * (s13 + s24) + R(4) * (s57 + s68);
+  const R c3 = R(1) / R(3), c6 = R(1) / R(6), c12 = R(1) / R(12);
+  const R ox = d13 * c6 - (d57 - d68) * c3;
+  const R oy = d24 * c6 - (d57 + d68) * c3;
+  const R o57 = d57 * c3 - (d13 + d24) * c12;
+  const R o68 = d68 * c3 - (d24 - d13) * c12;
+  const R ne0 = Q * (R(1) / R(9)), ne1 = Q * (R(-1) / R(18)), ne5 = Q * (R(1) / R(36));
+  const R fx = sigma * Sx * (R(1) / R(9)), fy = sigma * Sy * (R(1) / R(9));
+  const R f57 = sigma * (Sx + Sy) * (R(1) / R(36)), f68 = sigma * (Sy - Sx) * (R(1) / R(36));
+  f[0] = f[0] - omega * ne0;
+  f[1] = f[1] - omega * (ne1 + ox) + fx;
+  f[3] = f[3] - omega * (ne1 - ox) - fx;
+  f[2] = f[2] - omega * (ne1 + oy) + fy;
+  f[4] = f[4] - omega * (ne1 - oy) - fy;
+  f[5] = f[5] - omega * (ne5 + o57) + f57;
+  f[7] = f[7] - omega * (ne5 - o57) - f57;
+  f[6] = f[6] - omega * (ne5 + o68) + f68;
+  f[8] = f[8] - omega * (ne5 - o68) - f68;
 }
 
 // ------------------------------------------------------------------ tiles

@@ -1,0 +1,71 @@
+"""The kernels' collision is written in ghost combinations of the populations
+(one even, four odd) instead of moments and an equilibrium.  This pins that
+rewrite on the host: for random populations, sources and relaxation times it
+equals the oracle's literal BGK collision with forcing, Alg. 1 with Eq. feq and
+the forcing term, to double rounding.  The kernels run the same formulas; the
+GPU parity tests compare them with the oracle over whole histories."""
+import math
+
+import numpy as np
+import pytest
+
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+
+
+def literal(O, f, S, cs, tau, dt):
+    """Alg. 1 collision: moments of f, feq (Eq. feq) with j = sum c f + dt/2 S,
+    then g = f - (f - feq)/tau + (1 - 1/(2 tau)) psi dt."""
+    c = math.sqrt(3.0) * cs
+    r = f.sum()
+    j = np.array([c * (EX * f).sum() + 0.5 * dt * S[0], c * (EY * f).sum() + 0.5 * dt * S[1]])
+    Pi = np.array([(c * c * EX * EX * f).sum(), (c * c * EX * EY * f).sum(),
+                   (c * c * EY * EX * f).sum(), (c * c * EY * EY * f).sum()])
+    feq = O.equilibrium(cs, r, j, Pi)
+    psi = O.forcing(cs, S)
+    return f - (f - feq) / tau + (1.0 - 0.5 / tau) * psi * dt
+
+
+def ghost(f, S, cs, tau, dt):
+    """The kernels' form: g_q = f_q - omega (f - feq)_q + w_q sigma e_q.S."""
+    c = math.sqrt(3.0) * cs
+    omega, sigma = 1.0 / tau, c * dt / cs ** 2
+    s13, s24, s57, s68 = f[1] + f[3], f[2] + f[4], f[5] + f[7], f[6] + f[8]
+    d13, d24, d57, d68 = f[1] - f[3], f[2] - f[4], f[5] - f[7], f[6] - f[8]
+    Q = f[0] - 2 * (s13 + s24) + 4 * (s57 + s68)
+    ox, oy = d13 / 6 - (d57 - d68) / 3, d24 / 6 - (d57 + d68) / 3
+    o57, o68 = d57 / 3 - (d13 + d24) / 12, d68 / 3 - (d24 - d13) / 12
+    ne0, ne1, ne5 = Q / 9, -Q / 18, Q / 36
+    fx, fy = sigma * S[0] / 9, sigma * S[1] / 9
+    f57, f68 = sigma * (S[0] + S[1]) / 36, sigma * (S[1] - S[0]) / 36
+    g = np.empty(9)
+    g[0] = f[0] - omega * ne0
+    g[1], g[3] = f[1] - omega * (ne1 + ox) + fx, f[3] - omega * (ne1 - ox) - fx
+    g[2], g[4] = f[2] - omega * (ne1 + oy) + fy, f[4] - omega * (ne1 - oy) - fy
+    g[5], g[7] = f[5] - omega * (ne5 + o57) + f57, f[7] - omega * (ne5 - o57) - f57
+    g[6], g[8] = f[6] - omega * (ne5 + o68) + f68, f[8] - omega * (ne5 - o68) - f68
+    return g
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_ghost_form_equals_literal_collision(oracle_mod, seed):
+    rng = np.random.default_rng(seed)
+    f = rng.normal(0.0, 0.1, 9)
+    S = rng.normal(0.0, 1.0, 2)
+    cs = rng.uniform(0.3, 1.5)
+    tau = rng.uniform(0.51, 1.5)
+    dt = rng.uniform(0.01, 0.1)
+    ref = literal(oracle_mod, f, S, cs, tau, dt)
+    assert np.abs(ghost(f, S, cs, tau, dt) - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max())
+
+
+def test_ghost_form_conserves_r_pi_and_adds_dt_s(oracle_mod):
+    """Collision leaves r and Pi unchanged and adds dt S to c sum e f."""
+    rng = np.random.default_rng(7)
+    f, S, cs, tau, dt = rng.normal(0, 0.1, 9), rng.normal(0, 1, 2), 0.7, 0.55, 0.03
+    g = ghost(f, S, cs, tau, dt)
+    c = math.sqrt(3.0) * cs
+    assert abs(g.sum() - f.sum()) < 1e-15
+    for a, b in ((EX, EX), (EX, EY), (EY, EY)):
+        assert abs((a * b * (g - f)).sum()) < 1e-15
+    assert np.allclose([c * (EX * (g - f)).sum(), c * (EY * (g - f)).sum()], dt * S, atol=1e-15)
