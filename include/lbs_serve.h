@@ -13,6 +13,9 @@
  * its iteration count stops (its tiles return at once), is checked for
  * non-finite values, has u, v and P copied to host memory owned by the server
  * and its device memory released, after which queued requests are admitted.
+ * Every 1000 iterations (at the next scheduling point) each resident lattice
+ * is also checked for non-finite values; one that has some is retired at once
+ * as LBS_EUNSTABLE, like a handle whose monitor saw them.
  * Each lattice computes exactly what lbs_step computes for it alone.
  *
  * The server owns its device memory and its results until lbs_result hands

@@ -113,8 +113,24 @@ bool ensure(T *&ptr, int &cap, int need) {
   return true;
 }
 
+// iterations between the worker's checks for non-finite values (the same
+// interval as a handle's default monitor)
+constexpr int64_t kCheckEvery = 1000;
+
+// true if the lattice's state holds a non-finite value (brings the handle's
+// iteration and buffer parity up to date with the batch first)
+bool unstable(Req *r) {
+  lbs_handle *h = r->h;
+  h->k = r->k;
+  h->parity = (int)(r->k & 1);
+  h->kdev_value = -1;
+  lbs_monitors m;
+  return lbs_monitor(h, &m) == LBS_OK && m.nonfinite > 0;
+}
+
 void run(lbs_server *s) {
   cudaSetDevice(s->device);
+  int64_t since_check = 0;
   std::vector<Req *> res;
   std::vector<BatchLattice> hl;
   std::vector<BatchTile> ht;
@@ -216,11 +232,16 @@ void run(lbs_server *s) {
       s->st.launches += launched;
       for (Req *r : res) r->k = std::min(r->k + chunk, r->nsteps);
     }
-    // retire finished lattices
+    // retire finished lattices, and every kCheckEvery iterations those that
+    // went non-finite
+    since_check += chunk;
+    const bool check = since_check >= kCheckEvery;
+    if (check) since_check = 0;
     std::vector<Req *> keep;
     for (Req *r : res) {
       if (e != cudaSuccess) finish(s, r, LBS_ECUDA);
       else if (r->k >= r->nsteps) finish(s, r, LBS_OK);
+      else if (check && unstable(r)) finish(s, r, LBS_EUNSTABLE);
       else keep.push_back(r);
     }
     if (keep.size() != res.size()) dirty = true;
