@@ -128,9 +128,56 @@ bool unstable(Req *r) {
   return lbs_monitor(h, &m) == LBS_OK && m.nonfinite > 0;
 }
 
+// one chunk of `n` iterations of every resident lattice: replays of a CUDA
+// graph captured for the current tile tables (after one direct chunk on
+// them), else direct launches
+struct ChunkGraph {
+  cudaGraphExec_t exec = nullptr;
+  int64_t n = 0;
+  bool warm = false;  // one direct chunk ran on the current tables
+  void drop() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    n = 0;
+    warm = false;
+  }
+};
+
+cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int nres, int ni, int ne, int64_t n, ChunkGraph &G) {
+  auto direct = [&]() -> cudaError_t {
+    for (int64_t it = 0; it < n; ++it) {
+      const cudaError_t e = L.batch_step(s->d_lats, nres, s->d_tiles, ni, s->d_tiles + ni, ne, s->d_err, s->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  if (n != s->cfg.chunk || n < 2) return direct();
+  if (!G.warm) {
+    G.warm = true;
+    return direct();
+  }
+  if (!G.exec || G.n != n) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const cudaError_t e = direct();
+      const cudaError_t ec = cudaStreamEndCapture(s->stream, &g);
+      if (e == cudaSuccess && ec == cudaSuccess && g && cudaGraphInstantiate(&G.exec, g, 0) != cudaSuccess)
+        G.exec = nullptr;
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    G.n = G.exec ? n : 0;
+  }
+  if (!G.exec) return direct();
+  return cudaGraphLaunch(G.exec, s->stream);
+}
+
 void run(lbs_server *s) {
   cudaSetDevice(s->device);
   int64_t since_check = 0;
+  ChunkGraph graph;
   std::vector<Req *> res;
   std::vector<BatchLattice> hl;
   std::vector<BatchTile> ht;
@@ -178,6 +225,7 @@ void run(lbs_server *s) {
     if (res.empty()) continue;
     // batch tables
     if (dirty) {
+      graph.drop();
       hl.resize(res.size());
       ht.clear();
       std::vector<BatchTile> edge;
@@ -220,12 +268,10 @@ void run(lbs_server *s) {
     for (Req *r : res) longest = std::max(longest, r->nsteps - r->k);
     chunk = std::min(chunk, longest);
     const double tb = s->now();
-    int64_t launched = 0;
-    for (int64_t it = 0; it < chunk; ++it) {
-      L.batch_step(s->d_lats, (int)res.size(), s->d_tiles, ni, s->d_tiles + ni, ne, s->d_err, s->stream);
-      launched += (ni > 0) + (ne > 0) + 1;
-    }
-    const cudaError_t e = cudaStreamSynchronize(s->stream);
+    const int64_t launched = chunk * ((ni > 0) + (ne > 0) + 1);
+    cudaError_t e = run_chunk(s, L, (int)res.size(), ni, ne, chunk, graph);
+    const cudaError_t es = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = es;
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->st.busy_seconds += s->now() - tb;
@@ -248,6 +294,7 @@ void run(lbs_server *s) {
     res.swap(keep);
   }
   // shutdown: release what is still resident
+  graph.drop();
   for (Req *r : res) {
     if (r->h) lbs_destroy(r->h);
     r->h = nullptr;
