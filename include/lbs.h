@@ -208,6 +208,26 @@ int lbs_set_graph_chunk(lbs_handle *h, int32_t k);
  * default (the fastest on a large lattice); lbs_autotune picks per lattice. */
 int lbs_set_variant(lbs_handle *h, int32_t variant);
 
+/* ---- checkpoint / resume (no counterpart in the paper) ------------------
+ * A checkpoint is the state one iteration of Alg. 1 starts from: the
+ * distributions g, the displacement u and the boundary side array (N of the
+ * wall nodes), in the handle's storage precision, plus the iteration count and
+ * the lattice's parameters.  Resuming from it reproduces, bitwise, the
+ * iterations the saved handle would have run.
+ *
+ * lbs_checkpoint_bytes: size of the checkpoint of this handle (0 for NULL).
+ * lbs_save: waits for the handle's stream, then copies the state into
+ *   caller-owned host memory buf of at least that many bytes.  Errors:
+ *   LBS_EINVAL (NULL, buffer too small), LBS_EUNSTABLE / LBS_ETIMEOUT (as
+ *   lbs_sync), LBS_ECUDA.
+ * lbs_load: replaces the handle's state (and iteration count) with a
+ *   checkpoint taken from a handle created with the same lattice, material,
+ *   boundary set-up and precision (LBS_EINVAL otherwise, or for a truncated
+ *   buffer); clears the unstable flag; LBS_ECUDA on copy failure. */
+size_t lbs_checkpoint_bytes(const lbs_handle *h);
+int lbs_save(lbs_handle *h, void *buf, size_t bytes);
+int lbs_load(lbs_handle *h, const void *buf, size_t bytes);
+
 /* The handle's current tile variant (LBS_EINVAL for a null handle). */
 int32_t lbs_variant(const lbs_handle *h);
 

@@ -669,6 +669,77 @@ int lbs_autotune_handle(lbs_handle *h, int32_t steps) {
   return lbs_set_variant(h, best);
 }
 
+// ---- checkpoint / resume
+// Layout: CkptHeader, then g (nine planes of ny x pitch), u (ny x pitch
+// records), the boundary side array, each in the handle's storage format.
+namespace {
+struct CkptHeader {
+  char magic[8];        // "LBSCKPT1"
+  int32_t precision;
+  int32_t reserved;
+  int64_t k;            // iteration of the saved state
+  uint64_t g, u, b;     // bytes of each array
+  Params P;             // the lattice's parameters (must match on load)
+};
+const char kCkptMagic[8] = {'L', 'B', 'S', 'C', 'K', 'P', 'T', '1'};
+}  // namespace
+
+size_t lbs_checkpoint_bytes(const lbs_handle *h) {
+  if (!h) return 0;
+  const Sizes sz = sizes_of(h->P, *h->L);
+  return sizeof(CkptHeader) + sz.g + sz.u + sz.b;
+}
+
+int lbs_save(lbs_handle *h, void *buf, size_t bytes) {
+  if (!h || !buf) return fail(LBS_EINVAL, "null argument");
+  if (bytes < lbs_checkpoint_bytes(h)) return fail(LBS_EINVAL, "checkpoint buffer too small");
+  int rc = lbs_sync(h);
+  if (rc) return rc;
+  const Sizes sz = sizes_of(h->P, *h->L);
+  CkptHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, kCkptMagic, 8);
+  hd.precision = h->precision;
+  hd.k = h->k;
+  hd.g = sz.g;
+  hd.u = sz.u;
+  hd.b = sz.b;
+  hd.P = h->P;
+  char *out = (char *)buf;
+  memcpy(out, &hd, sizeof(hd));
+  out += sizeof(hd);
+  LBS_CK(cudaMemcpy(out, h->g[h->parity], sz.g, cudaMemcpyDeviceToHost));
+  LBS_CK(cudaMemcpy(out + sz.g, h->u[h->parity], sz.u, cudaMemcpyDeviceToHost));
+  LBS_CK(cudaMemcpy(out + sz.g + sz.u, h->b[h->parity], sz.b, cudaMemcpyDeviceToHost));
+  return LBS_OK;
+}
+
+int lbs_load(lbs_handle *h, const void *buf, size_t bytes) {
+  if (!h || !buf) return fail(LBS_EINVAL, "null argument");
+  if (bytes < sizeof(CkptHeader)) return fail(LBS_EINVAL, "checkpoint too short");
+  CkptHeader hd;
+  memcpy(&hd, buf, sizeof(hd));
+  const Sizes sz = sizes_of(h->P, *h->L);
+  if (memcmp(hd.magic, kCkptMagic, 8) != 0) return fail(LBS_EINVAL, "not a liblbs checkpoint");
+  if (hd.precision != h->precision || hd.g != sz.g || hd.u != sz.u || hd.b != sz.b ||
+      memcmp(&hd.P, &h->P, sizeof(Params)) != 0)
+    return fail(LBS_EINVAL, "checkpoint of a different lattice, material, boundary set-up or precision");
+  if (bytes < sizeof(CkptHeader) + sz.g + sz.u + sz.b || hd.k < 0) return fail(LBS_EINVAL, "checkpoint truncated");
+  LBS_CK(cudaStreamSynchronize(h->stream));
+  const char *in = (const char *)buf + sizeof(CkptHeader);
+  LBS_CK(cudaMemcpy(h->g[h->parity], in, sz.g, cudaMemcpyHostToDevice));
+  LBS_CK(cudaMemcpy(h->u[h->parity], in + sz.g, sz.u, cudaMemcpyHostToDevice));
+  LBS_CK(cudaMemcpy(h->b[h->parity], in + sz.g + sz.u, sz.b, cudaMemcpyHostToDevice));
+  h->k = hd.k;
+  h->kdev_value = -1;  // graph replays re-read the iteration base
+  h->unstable_at = -1;
+  h->mon_pending = false;
+  h->next_mon = h->mon_interval > 0 ? (h->k / h->mon_interval + 1) * h->mon_interval : 0;
+  LBS_CK(cudaMemsetAsync(h->mon_out, 0, 7 * sizeof(double), h->stream));
+  LBS_CK(cudaStreamSynchronize(h->stream));
+  return LBS_OK;
+}
+
 int64_t lbs_iteration(const lbs_handle *h) { return h ? h->k : -1; }
 int64_t lbs_unstable_iteration(const lbs_handle *h) { return h ? h->unstable_at : -1; }
 int lbs_cfl_warning(const lbs_handle *h) { return h ? h->cfl_warn : 0; }

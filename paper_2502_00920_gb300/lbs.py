@@ -95,6 +95,9 @@ SIGNATURES = {
     "lbs_tile_variant_kind": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     "lbs_tile_variant_name": (ctypes.c_char_p, [ctypes.c_int32, ctypes.c_int32]),
     "lbs_variant": (ctypes.c_int32, [_vp]),
+    "lbs_checkpoint_bytes": (ctypes.c_size_t, [_vp]),
+    "lbs_save": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_size_t]),
+    "lbs_load": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_size_t]),
     "lbs_set_allocator": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbs_autotune": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(Material), ctypes.POINTER(Bcs),
                                     ctypes.c_int32, _i32p, ctypes.POINTER(ctypes.c_float)]),
@@ -331,6 +334,17 @@ class Simulation:
     @property
     def variant(self) -> int:
         return int(lib().lbs_variant(self._h))
+
+    # -- checkpoint / resume
+    def save(self) -> np.ndarray:
+        """The state (g, u, boundary side array, iteration) as a uint8 array."""
+        buf = np.empty(int(lib().lbs_checkpoint_bytes(self._h)), dtype=np.uint8)
+        check(lib().lbs_save(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes))
+        return buf
+
+    def load(self, buf: np.ndarray):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(lib().lbs_load(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes))
 
     # -- outputs
     def fields(self, u=True, v=True, P=True):
