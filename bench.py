@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -312,7 +313,23 @@ def suite(args):
         sim.close()
         return out, dt, unstable, np.array(hist)
 
+    want = lambda part: args.suite_parts == "all" or part in args.suite_parts.split(",")
     # tension 32x32, neo-Hooke, 2000 iterations
+    if want("tension"):
+        suite_tension(args, L, I, O, emit, gpu_run, rel)
+    if want("shear"):
+        suite_shear(args, L, I, O, emit, gpu_run, rel)
+    if want("cantilever"):
+        suite_cantilever(args, L, I, O, emit, gpu_run, rel)
+    if want("paper"):
+        suite_paper(args, L, I, O, emit, gpu_run, rel)
+    if want("serving"):
+        emit(config="serving", **serving(L, I, args.serving_requests_suite, args.suite_serving_steps_scale))
+    if want("roofline"):
+        suite_roofline(args, L, I, torch, dev, emit)
+
+
+def suite_tension(args, L, I, O, emit, gpu_run, rel):
     case = I.tension()
     ora = O.OracleSim(case)
     ora_hist, k_nan = {}, None
@@ -332,6 +349,9 @@ def suite(args):
                  u_err=rel(u, ur) if fin and np.isfinite(u).all() else None,
                  P_err=rel(P, Pr) if fin and np.isfinite(P).all() else None,
                  P11_interior=float(P[8:24, 8:24, 0].mean()) if np.isfinite(P).all() else None)
+
+
+def suite_shear(args, L, I, O, emit, gpu_run, rel):
     # simple shear 256^2, SVK, six Poisson ratios, 20k iterations
     nsh = args.suite_shear_steps
     for nu in (0.0, 0.1, 0.2, 0.3, 0.4, 0.45):
@@ -345,6 +365,9 @@ def suite(args):
             emit(config="shear_256_svk", nu=nu, precision=prec, iterations=nsh, mlups=256 * 256 * nsh / dt / 1e6,
                  unstable_gpu=unstable, oracle_finite=bool(np.isfinite(ur).all()),
                  u_err=rel(u, ur) if fin else None, P_err=rel(P, Pr) if fin else None)
+
+
+def suite_cantilever(args, L, I, O, emit, gpu_run, rel):
     # cantilever 4096x256, 100k iterations, tip history every 100 iterations
     nc = args.suite_cantilever_steps
     case = I.cantilever(4096, 256, nc)
@@ -379,8 +402,41 @@ def suite(args):
         ug = s.fields()[0]
     emit(config="cantilever_4096x256", precision="fp64", iterations=args.suite_cantilever_prefix,
          u_err_vs_oracle=rel(ug, o.fields()[0]))
-    # batched serving
-    emit(config="serving", **serving(L, I, args.serving_requests_suite, args.suite_serving_steps_scale))
+
+
+def suite_paper(args, L, I, O, emit, gpu_run, rel):
+    # the paper's examples at its own sizes against the oracle over their
+    # horizons, and a refinement ladder (self-convergence on the GPU, FP64)
+    for name, case, T in (("paper_tension_nh_0.3", I.paper_tension("nh", 0.3), 2.2),
+                          ("paper_shear_svk_0.2", I.paper_shear("svk", 0.2), 2.2),
+                          ("paper_wave_tau0.55", I.paper_wave(0.55), 12.0)):
+        steps = int(round(T / O.params(case)["dt"]))
+        (u, v, P), dt, unstable, _ = gpu_run(case, steps)
+        o = O.OracleSim(case)
+        o.step(steps)
+        ur, vr, Pr = o.fields()
+        emit(config=name, precision="fp64", nx=case.nx, ny=case.ny, iterations=steps, unstable_gpu=unstable,
+             u_err=rel(u, ur), v_err=rel(v, vr), P_err=rel(P, Pr), max_abs_u=float(np.abs(ur).max()))
+    for name, mk in (("tension_nh_0.3", lambda n: I.paper_tension("nh", 0.3, n=n)),
+                     ("shear_svk_0.2", lambda n: I.paper_shear("svk", 0.2, n=n))):
+        c20 = mk(20)
+        K = int(round(2.2 / O.params(c20)["dt"]))  # iterations at n = 20; n = 20 * 2^m runs K * 2^m
+        us = []
+        for m in range(5):
+            n = 20 * 2 ** m
+            (u, _, _), dt, unstable, _ = gpu_run(mk(n), K * 2 ** m)
+            us.append(u)
+        diffs = []
+        for m in range(4):
+            f = us[m + 1]
+            restricted = 0.25 * (f[0::2, 0::2] + f[1::2, 0::2] + f[0::2, 1::2] + f[1::2, 1::2])
+            diffs.append(float(np.abs(restricted - us[m]).max()))
+        orders = [math.log2(diffs[m] / diffs[m + 1]) for m in range(3)]
+        emit(config=f"paper_refinement_{name}", precision="fp64", n=[20 * 2 ** m for m in range(5)],
+             t=K * O.params(c20)["dt"], diff_to_next=diffs, observed_order=orders)
+
+
+def suite_roofline(args, L, I, torch, dev, emit):
     # roofline 16384^2, 500 iterations
     case = I.roofline(n=16384, nsteps=500)
     v0 = I.grf_velocity(case, device=dev)
@@ -418,6 +474,8 @@ def main():
     ap.add_argument("--suite-cantilever-prefix", type=int, default=1000)
     ap.add_argument("--serving-requests-suite", type=int, default=512)
     ap.add_argument("--suite-serving-steps-scale", type=float, default=1.0)
+    ap.add_argument("--suite-parts", default="all",
+                    help="comma list of tension,shear,cantilever,paper,serving,roofline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

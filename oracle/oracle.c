@@ -336,7 +336,20 @@ void ora_load(const ora_config *cfg, int edge, long k, double out[2]) {
 
 /* quasi-boundary traction on a wall with outward unit normal N:
  *   Pi* N = -T* + (P + Pi(H)) N  ->  first row and column of Pi* */
-static void wall_flux_column(const ora_sim *s, long i, int edge, double col[2]) {
+/* The value of a node field carried to the wall(s) a link crosses (reading
+ * R7 and its linear variant): the node's own value, or under
+ * ORA_EXTRAP_LINEAR v + (v - v_in)/2 for each crossed wall, v_in the value at
+ * the next node inwards along that wall's normal. */
+static double at_wall(const ora_sim *s, const double *a, int x, int y, int wx, int wy) {
+  double v = a[node(s, x, y)];
+  if (s->cfg.extrap != ORA_EXTRAP_LINEAR) return v;
+  double e = v;
+  if (wx >= 0) e += 0.5 * (v - a[node(s, wx == ORA_LEFT ? x + 1 : x - 1, y)]);
+  if (wy >= 0) e += 0.5 * (v - a[node(s, x, wy == ORA_BOTTOM ? y + 1 : y - 1)]);
+  return e;
+}
+
+static void wall_flux_column(const ora_sim *s, int x, int y, int edge, int wx, int wy, double col[2]) {
   long n = s->n;
   double Nv[2] = {0.0, 0.0};
   if (edge == ORA_LEFT) Nv[0] = -1.0;
@@ -347,7 +360,8 @@ static void wall_flux_column(const ora_sim *s, long i, int edge, double col[2]) 
   ora_load(&s->cfg, edge, s->k, T);
   mat2 NP;
   for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b) NP[a][b] = s->P[(2 * a + b) * n + i] + s->Ph[(2 * a + b) * n + i];
+    for (int b = 0; b < 2; ++b)
+      NP[a][b] = at_wall(s, s->P + (2 * a + b) * n, x, y, wx, wy) + at_wall(s, s->Ph + (2 * a + b) * n, x, y, wx, wy);
   int nd = (edge == ORA_LEFT || edge == ORA_RIGHT) ? 0 : 1;
   for (int a = 0; a < 2; ++a) {
     double q = -T[a] + NP[a][0] * Nv[0] + NP[a][1] * Nv[1];
@@ -355,15 +369,15 @@ static void wall_flux_column(const ora_sim *s, long i, int edge, double col[2]) 
   }
 }
 
-static void neumann_flux(const ora_sim *s, long i, int xwall, int ywall, mat2 Pis) {
+static void neumann_flux(const ora_sim *s, int x, int y, int xwall, int ywall, mat2 Pis) {
   long n = s->n;
   /* start from the node's own moment (extrapolated entries) */
-  Pis[0][0] = s->Pi[0 * n + i];
-  Pis[0][1] = Pis[1][0] = s->Pi[1 * n + i];
-  Pis[1][1] = s->Pi[2 * n + i];
+  Pis[0][0] = at_wall(s, s->Pi + 0 * n, x, y, xwall, ywall);
+  Pis[0][1] = Pis[1][0] = at_wall(s, s->Pi + 1 * n, x, y, xwall, ywall);
+  Pis[1][1] = at_wall(s, s->Pi + 2 * n, x, y, xwall, ywall);
   double cx[2], cy[2];
-  if (xwall >= 0) wall_flux_column(s, i, xwall, cx);
-  if (ywall >= 0) wall_flux_column(s, i, ywall, cy);
+  if (xwall >= 0) wall_flux_column(s, x, y, xwall, xwall, ywall, cx);
+  if (ywall >= 0) wall_flux_column(s, x, y, ywall, xwall, ywall, cy);
   if (xwall >= 0 && ywall >= 0) {
     Pis[0][0] = cx[0];
     Pis[1][1] = cy[1];
@@ -397,6 +411,7 @@ static int validate(const ora_config *c) {
     if (ed->time_unit != 0 && ed->time_unit != 1) return 0;
   }
   if (c->order != ORA_ORDER_TEXT && c->order != ORA_ORDER_LISTING) return 0;
+  if (c->extrap != ORA_EXTRAP_OWN && c->extrap != ORA_EXTRAP_LINEAR) return 0;
   if ((c->edge[ORA_LEFT].type == ORA_PERIODIC) != (c->edge[ORA_RIGHT].type == ORA_PERIODIC)) return 0;
   if ((c->edge[ORA_BOTTOM].type == ORA_PERIODIC) != (c->edge[ORA_TOP].type == ORA_PERIODIC)) return 0;
   return 1;
@@ -572,8 +587,8 @@ static void block2_boundaries(ora_sim *s) {
           /* Eq. (abbcon): f_qbar = -f_q^coll + 2 w_q (r + (Pi* - r cs^2 I):(c c - cs^2 I)/(2 cs^4)) */
           /* Pi* from the wall(s) this link crosses */
           mat2 Pis;
-          neumann_flux(s, i, wx, wy, Pis);
-          double rbd = s->r[i];
+          neumann_flux(s, x, y, wx, wy, Pis);
+          double rbd = at_wall(s, s->r, x, y, wx, wy);
           double contr = 0.0;
           for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)

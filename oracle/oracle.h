@@ -44,6 +44,13 @@ enum {
  * printed, so the collision at t uses S(u(t - dt)); kept only to show that
  * this order is unstable for nu > 1/4 even on a periodic lattice. */
 enum { ORA_ORDER_TEXT = 0, ORA_ORDER_LISTING = 1 };
+/* How the Neumann rule's r^bd, the node's own Pi entries and P + Pi(H) are
+ * carried to the wall, which lies half a spacing beyond the boundary node
+ * (Sect. 3.3, "extrapolated to the boundary").  OWN: the boundary node's
+ * value (zeroth order; the default).  LINEAR: v + (v - v_in)/2 along the
+ * normal of each wall the link crosses, v_in the value at the next node
+ * inwards (both walls' terms at a corner). */
+enum { ORA_EXTRAP_OWN = 0, ORA_EXTRAP_LINEAR = 1 };
 enum { ORA_LEFT = 0, ORA_RIGHT = 1, ORA_BOTTOM = 2, ORA_TOP = 3 };
 
 typedef struct {
@@ -63,6 +70,7 @@ typedef struct {
   double body[2]; /* body force density b                                  */
   ora_edge edge[4]; /* left (-x), right (+x), bottom (-y), top (+y)        */
   int order;      /* ORA_ORDER_TEXT (default) or ORA_ORDER_LISTING, below   */
+  int extrap;     /* ORA_EXTRAP_OWN (default) or ORA_EXTRAP_LINEAR, below    */
 } ora_config;
 
 typedef struct ora_sim ora_sim;

@@ -49,7 +49,7 @@ class _Config(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double), ("tau", ctypes.c_double),
                 ("model", ctypes.c_int), ("E", ctypes.c_double), ("nu", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("body", ctypes.c_double * 2), ("edge", _Edge * 4),
-                ("order", ctypes.c_int)]
+                ("order", ctypes.c_int), ("extrap", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -91,11 +91,13 @@ def _f64(a, shape=None):
 
 
 ORDER = {"text": 0, "listing": 1}
+EXTRAP = {"own": 0, "linear": 1}
 
 
 def config(case, order: str = "text") -> _Config:
     c = _Config()
     c.order = ORDER[order]
+    c.extrap = EXTRAP[getattr(case, "extrap", "own")]
     c.nx, c.ny = int(case.nx), int(case.ny)
     c.dx = float(case.dx if case.dx is not None else 1.0 / case.ny)
     c.tau = float(case.tau)

@@ -68,6 +68,7 @@ class Case:
     init: str = "rest"  # "rest" | "grf" | "translation" | "custom"
     seed: int = 0
     init_args: dict = field(default_factory=dict, hash=False, compare=False)
+    extrap: str = "own"  # Neumann wall values: "own" (boundary node) | "linear" (two-point)
 
     @property
     def spacing(self) -> float:

@@ -171,6 +171,9 @@ def _ptr(a: np.ndarray):
 
 def structs(case):
     """(Lattice, Material, Bcs) of a Case."""
+    if getattr(case, "extrap", "own") != "own":
+        raise ValueError("liblbs carries the boundary node's own values to the wall; the two-point linear "
+                         "extrapolation exists in the oracle only")
     lat = Lattice(int(case.nx), int(case.ny), float(case.dx if case.dx is not None else 1.0 / case.ny),
                   float(case.tau), PRECISION[case.precision], int(getattr(case, "gscale_log2", 0) or 0))
     mat = Material(MODEL[case.model], float(case.E), float(case.nu), float(case.rho0),

@@ -464,3 +464,39 @@ def test_linear_material_scales_linearly(oracle_mod):
     _, (u2, _, _) = run(oracle_mod, dbl, None, None, 60)
     assert np.abs(u1).max() > 1e-6
     np.testing.assert_allclose(u2, 2 * u1, rtol=0, atol=1e-13 * np.abs(u2).max())
+
+
+def homogeneous_case(I, O, model, extrap, nx=24, ny=16):
+    """A block under a uniform deformation F with every edge loaded by the
+    traction P(F) N of its outward normal N (Cauchy's relation): the exact
+    solution is static, u = (F - I) X, P = P(F) everywhere."""
+    base = I.Case("h", nx, ny, 0, model=model, nu=0.2)
+    prm = O.params(base)
+    H = np.array([[0.06, 0.02], [-0.01, -0.03]])
+    P = O.first_piola(model, prm["lam"], prm["mu"], H).reshape(2, 2)
+    T = lambda n: tuple(float(v) for v in P @ np.array(n, float))
+    edges = (I.Edge("neumann", "const", T((-1, 0))), I.Edge("neumann", "const", T((1, 0))),
+             I.Edge("neumann", "const", T((0, -1))), I.Edge("neumann", "const", T((0, 1))))
+    case = base.replace(edges=edges, extrap=extrap)
+    dx = case.spacing
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dx)
+    u0 = np.stack([H[0, 0] * X + H[0, 1] * Y, H[1, 0] * X + H[1, 1] * Y], -1)
+    return case, u0, P
+
+
+@pytest.mark.parametrize("model", ["svk", "nh", "le"])
+@pytest.mark.parametrize("extrap", ["own", "linear"])
+def test_homogeneous_stress_under_its_traction_is_static(oracle_mod, model, extrap):
+    """Pins the Neumann rule (Eq. abbcon with Pi* from -T* + (P + Pi(H)) N),
+    the one-sided wall differences, the initial equilibrium with Pi(H0) and
+    the zero source of a uniform stress: a wrong sign of T*, a transposed
+    normal column or a missing Pi(H) term sets the block in motion.  Both
+    readings of the wall extrapolation agree here (uniform fields)."""
+    from paper_2502_00920_gb300 import inputs as I
+    case, u0, P = homogeneous_case(I, oracle_mod, model, extrap)
+    s = oracle_mod.OracleSim(case, u0, None)
+    s.step(200)
+    u, v, Pf = s.fields()
+    assert np.abs(u - u0).max() <= 1e-13
+    assert np.abs(v).max() <= 1e-13
+    assert np.abs(Pf - P.reshape(4)).max() <= 1e-13

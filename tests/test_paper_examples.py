@@ -37,3 +37,17 @@ def test_paper_bending_wave_stays_bounded(oracle_mod, tau):
     u, v, P = run_to(oracle_mod, I.paper_wave(tau), 12.0)
     assert np.isfinite(u).all() and np.abs(u).max() < 0.6
     assert np.abs(u[:, 0]).max() == 0.0 or np.abs(u[:, 0]).max() < 0.05  # clamped end stays near rest
+
+
+def test_linear_wall_extrapolation_is_unstable_on_the_bending_wave(oracle_mod):
+    """Reading R7 takes the boundary node's own values for r^bd, Pi and
+    P + Pi(H) at the wall.  The two-point linear extrapolation, the other
+    reading of "extrapolated to the boundary" in Sect. 3.3, changes the 40 x 40
+    tension result by under 1 % but makes the paper's bending wave go
+    non-finite before t = 12, which the paper runs without blow-up."""
+    u_own = run_to(oracle_mod, I.paper_tension("nh", 0.3), 2.2)[0]
+    u_lin = run_to(oracle_mod, I.paper_tension("nh", 0.3).replace(extrap="linear"), 2.2)[0]
+    assert np.isfinite(u_lin).all()
+    assert np.abs(u_lin - u_own).max() < 0.01 * np.abs(u_own).max()
+    assert np.isfinite(run_to(oracle_mod, I.paper_wave(0.55), 12.0)[0]).all()
+    assert not np.isfinite(run_to(oracle_mod, I.paper_wave(0.55).replace(extrap="linear"), 12.0)[0]).all()

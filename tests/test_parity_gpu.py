@@ -345,3 +345,44 @@ def test_tension_32_full_history(L, oracle_mod):
         u = s.fields()[0]
     ur = run_oracle(oracle_mod, case, 1000)[0]
     assert rel(u, ur) <= 1e-12
+
+
+def paper_cases():
+    """The paper's own examples at its lattice sizes (Sect. 4): 40 x 40
+    tension and shear to t = 2.2, the 160 x 40 bending wave to t = 12."""
+    return {
+        "paper_tension_nh_0.3": (I.paper_tension("nh", 0.3), 2.2),
+        "paper_tension_svk_0.25": (I.paper_tension("svk", 0.25), 2.2),
+        "paper_shear_nh_0.3": (I.paper_shear("nh", 0.3), 2.2),
+        "paper_shear_svk_0.2": (I.paper_shear("svk", 0.2), 2.2),
+        "paper_wave_tau0.55": (I.paper_wave(0.55), 12.0),
+        "paper_wave_tau0.59": (I.paper_wave(0.59), 12.0),
+    }
+
+
+@pytest.mark.parametrize("name", list(paper_cases()))
+def test_paper_examples_match_oracle(L, oracle_mod, name):
+    """GPU FP64 against the oracle over the paper's whole horizon, with the
+    loads given in the paper's time unit."""
+    case, T = paper_cases()[name]
+    steps = int(round(T / oracle_mod.params(case)["dt"]))
+    u, v, P = run_gpu(L, case, steps)
+    ur, vr, Pr = run_oracle(oracle_mod, case, steps)
+    record(f"fp64/{name}", u=rel(u, ur), v=rel(v, vr), P=rel(P, Pr))
+    assert np.isfinite(ur).all() and np.abs(ur).max() > 1e-4
+    assert rel(u, ur) <= TOL["fp64"], rel(u, ur)
+    assert rel(v, vr) <= TOL["fp64"], rel(v, vr)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6), ("fp16s", 1e-3)])
+@pytest.mark.parametrize("model", ["svk", "nh"])
+def test_homogeneous_stress_under_its_traction_is_static(L, oracle_mod, model, precision, tol):
+    """A block under uniform F with every edge loaded by P(F) N stays at
+    u = (F - I) X with P = P(F) (the exact static solution; the oracle is
+    pinned to it on the host)."""
+    from test_oracle_pins import homogeneous_case
+    case, u0, P = homogeneous_case(I, oracle_mod, model, "own")
+    u, v, Pf = run_gpu(L, case.replace(precision=precision), 200, u0, None)
+    scale = np.abs(u0).max()
+    assert np.abs(u - u0).max() <= tol * scale
+    assert np.abs(Pf - P.reshape(4)).max() <= tol * 10 * np.abs(P).max()
