@@ -180,32 +180,35 @@ def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: floa
     [0, 0.45], tension / shear / tip-pulse loads, iterations log-uniform
     1k..50k scaled by steps_scale).
 
-    The one-at-a-time FP64 baseline runs every request alone (create, step,
-    fetch fields, destroy) and records its service time; its FIFO queue under
-    the arrival times is then exact: done_i = max(arrival_i, done_{i-1}) +
-    service_i.  Arrivals are Poisson at `load` times that baseline's capacity.
-    The FP32 server then receives the same arrivals in real time (latency
-    p50/p99), and, on a fresh server, the whole trace at once (capacity:
-    node updates / makespan, against the baseline's node updates / total
-    service time).  A request has failed if the library reported it unstable
-    or its final u holds a non-finite value.  Every request finite in both
-    arms states its FP32 error on u against its FP64 result."""
+    The one-at-a-time FP64 baseline runs every request alone (create, step in
+    chunks of 1000 iterations, fetch fields, destroy) and records its service
+    time; its FIFO queue under the arrival times is then exact: done_i =
+    max(arrival_i, done_{i-1}) + service_i.  Arrivals are Poisson at `load`
+    times that baseline's capacity.  The FP32 server then receives the same
+    arrivals in real time (latency p50/p99), and, on a fresh server, the whole
+    trace at once (capacity).  Both arms stop a request that went non-finite
+    at their next 1000-iteration check and count it as failed (also when its
+    final u is not finite); aggregate MLUPS counts the node updates actually
+    executed.  Every request finite in both arms states its FP32 error on u
+    against its FP64 result."""
     import threading
     trace = I.serving_trace(n_requests, seed=seed, rate=1.0)
     cases = [c.replace(nsteps=max(100, int(round(c.nsteps * steps_scale)))) for _, c in trace]
     work = [c.nx * c.ny * c.nsteps for c in cases]
     # one at a time, FP64
-    service, u64 = [], []
+    service, u64, done64 = [], [], 0
     for c in cases:
         t0 = time.perf_counter()
         u = None
-        try:
-            with L.Simulation(c.replace(precision="fp64")) as s:
-                s.step(c.nsteps)
-                s.sync()
+        with L.Simulation(c.replace(precision="fp64")) as s:
+            try:
+                while s.iteration < c.nsteps:
+                    s.step(min(1000, c.nsteps - s.iteration))
+                    s.sync()  # the chunk's monitor: stops a request that went non-finite
                 u, _, _ = s.fields(True, True, True)
-        except L.LbsError:
-            pass
+            except L.LbsError:
+                pass
+            done64 += c.nx * c.ny * s.iteration
         service.append(time.perf_counter() - t0)
         u64.append(u if u is not None and np.isfinite(u).all() else None)
     capacity = len(cases) / sum(service)
@@ -217,7 +220,7 @@ def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: floa
         t = max(a, t) + sv
         done.append(t)
     seq_ttr = [d - a for d, a in zip(done, arrivals)]
-    q = lambda xs, p: sorted(xs)[min(len(xs) - 1, int(round(p * (len(xs) - 1))))]
+    q = lambda xs, p: sorted(xs)[min(len(xs) - 1, int(round(p * (len(xs) - 1))))] if xs else None
 
     def collect(srv, tickets):
         infos = [srv.poll(tk) for tk in tickets]
@@ -253,18 +256,27 @@ def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: floa
         tickets = [srv.submit(c.replace(precision="fp32")) for c in cases]
         srv.drain(-1)
         makespan = time.perf_counter() - t0
+        sat_stats = srv.stats()
         sat_infos, sat_u = collect(srv, tickets)
+    ok = [u is not None for u in u64]
     errs = [float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
             for a, b in zip(u32, u64) if a is not None and b is not None]
-    return {"requests": len(cases), "steps_scale": steps_scale, "node_updates": sum(work),
+    return {"requests": len(cases), "steps_scale": steps_scale, "node_updates_requested": sum(work),
             "offered_load_x_fp64_capacity": load, "arrival_rate_per_s": rate,
-            "sequential_fp64": {"aggregate_mlups": sum(work) / sum(service) / 1e6,
+            "sequential_fp64": {"aggregate_mlups": done64 / sum(service) / 1e6, "node_updates": done64,
                                 "p50_s": q(seq_ttr, 0.5), "p99_s": q(seq_ttr, 0.99),
+                                "p50_s_completed": q([x for x, o in zip(seq_ttr, ok) if o], 0.5),
+                                "p99_s_completed": q([x for x, o in zip(seq_ttr, ok) if o], 0.99),
                                 "failed": sum(u is None for u in u64), "service_s": sum(service)},
-            "batched_fp32_poisson": {"aggregate_mlups": sum(work) / span / 1e6, "p50_s": q(ttr, 0.5),
-                                     "p99_s": q(ttr, 0.99), "failed": sum(u is None for u in u32),
+            "batched_fp32_poisson": {"aggregate_mlups": stats["node_updates"] / span / 1e6,
+                                     "node_updates": stats["node_updates"], "p50_s": q(ttr, 0.5),
+                                     "p99_s": q(ttr, 0.99),
+                                     "p50_s_completed": q([x for x, u in zip(ttr, u32) if u is not None], 0.5),
+                                     "p99_s_completed": q([x for x, u in zip(ttr, u32) if u is not None], 0.99),
+                                     "failed": sum(u is None for u in u32),
                                      "launches": stats["launches"], "busy_s": stats["busy_seconds"]},
-            "batched_fp32_saturated": {"aggregate_mlups": sum(work) / makespan / 1e6, "makespan_s": makespan,
+            "batched_fp32_saturated": {"aggregate_mlups": sat_stats["node_updates"] / makespan / 1e6,
+                                       "node_updates": sat_stats["node_updates"], "makespan_s": makespan,
                                        "failed": sum(u is None for u in sat_u),
                                        "equal_to_poisson_run": all(
                                            (a is None and b is None) or (a is not None and b is not None
@@ -313,12 +325,44 @@ def suite(args):
         sim.close()
         return out, dt, unstable, np.array(hist)
 
+    def first_nonfinite_gpu(case, steps):
+        """First iteration whose state holds a non-finite value (GPU FP64, a
+        monitor after every iteration), or None."""
+        sim = L.Simulation(case.replace(precision="fp64"), monitor_interval=1, graph_chunk=0)
+        try:
+            sim.step(steps)
+            sim.sync()
+        except L.LbsError:
+            pass
+        k = sim.unstable_iteration
+        sim.close()
+        return None if k < 0 else k
+
+    def first_nonfinite_oracle(case, steps, coarse=50):
+        """(first iteration whose u, v or P is non-finite or None, fields after
+        `steps` iterations if they stayed finite)."""
+        finite = lambda f: all(np.isfinite(a).all() for a in f)
+        o = O.OracleSim(case)
+        k = 0
+        while k < steps:
+            n = min(coarse, steps - k)
+            o.step(n)
+            k += n
+            if not finite(o.fields()):
+                o = O.OracleSim(case)
+                o.step(k - n)
+                for kk in range(k - n + 1, k + 1):
+                    o.step(1)
+                    if not finite(o.fields()):
+                        return kk, None
+        return None, o.fields()
+
     want = lambda part: args.suite_parts == "all" or part in args.suite_parts.split(",")
     # tension 32x32, neo-Hooke, 2000 iterations
     if want("tension"):
-        suite_tension(args, L, I, O, emit, gpu_run, rel)
+        suite_tension(args, L, I, O, emit, gpu_run, rel, first_nonfinite_gpu, first_nonfinite_oracle)
     if want("shear"):
-        suite_shear(args, L, I, O, emit, gpu_run, rel)
+        suite_shear(args, L, I, O, emit, gpu_run, rel, first_nonfinite_gpu, first_nonfinite_oracle)
     if want("cantilever"):
         suite_cantilever(args, L, I, O, emit, gpu_run, rel)
     if want("paper"):
@@ -329,8 +373,10 @@ def suite(args):
         suite_roofline(args, L, I, torch, dev, emit)
 
 
-def suite_tension(args, L, I, O, emit, gpu_run, rel):
+def suite_tension(args, L, I, O, emit, gpu_run, rel, first_nonfinite_gpu, first_nonfinite_oracle):
     case = I.tension()
+    emit(config="tension_32x32_nh", first_nonfinite_oracle=first_nonfinite_oracle(case, 2000)[0],
+         first_nonfinite_gpu_fp64=first_nonfinite_gpu(case, 2000))
     ora = O.OracleSim(case)
     ora_hist, k_nan = {}, None
     for k in range(0, 2000, 50):
@@ -351,20 +397,20 @@ def suite_tension(args, L, I, O, emit, gpu_run, rel):
                  P11_interior=float(P[8:24, 8:24, 0].mean()) if np.isfinite(P).all() else None)
 
 
-def suite_shear(args, L, I, O, emit, gpu_run, rel):
+def suite_shear(args, L, I, O, emit, gpu_run, rel, first_nonfinite_gpu, first_nonfinite_oracle):
     # simple shear 256^2, SVK, six Poisson ratios, 20k iterations
     nsh = args.suite_shear_steps
     for nu in (0.0, 0.1, 0.2, 0.3, 0.4, 0.45):
         case = I.shear(256, nsh, model="svk", nu=nu)
-        o = O.OracleSim(case)
-        o.step(nsh)
-        ur, vr, Pr = o.fields()
+        k_o, fo = first_nonfinite_oracle(case, nsh)
+        emit(config="shear_256_svk", nu=nu, first_nonfinite_oracle=k_o,
+             first_nonfinite_gpu_fp64=first_nonfinite_gpu(case, nsh))
         for prec in ("fp64", "fp32", "fp16s"):
             (u, v, P), dt, unstable, _ = gpu_run(case.replace(precision=prec), nsh, monitor=1000)
-            fin = np.isfinite(ur).all() and np.isfinite(u).all()
+            fin = fo is not None and np.isfinite(u).all()
             emit(config="shear_256_svk", nu=nu, precision=prec, iterations=nsh, mlups=256 * 256 * nsh / dt / 1e6,
-                 unstable_gpu=unstable, oracle_finite=bool(np.isfinite(ur).all()),
-                 u_err=rel(u, ur) if fin else None, P_err=rel(P, Pr) if fin else None)
+                 unstable_gpu=unstable, oracle_finite=fo is not None,
+                 u_err=rel(u, fo[0]) if fin else None, P_err=rel(P, fo[2]) if fin else None)
 
 
 def suite_cantilever(args, L, I, O, emit, gpu_run, rel):

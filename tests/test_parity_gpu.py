@@ -374,7 +374,7 @@ def test_paper_examples_match_oracle(L, oracle_mod, name):
     assert rel(v, vr) <= TOL["fp64"], rel(v, vr)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6), ("fp16s", 1e-3)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6), ("fp16s", 1e-2)])
 @pytest.mark.parametrize("model", ["svk", "nh"])
 def test_homogeneous_stress_under_its_traction_is_static(L, oracle_mod, model, precision, tol):
     """A block under uniform F with every edge loaded by P(F) N stays at
@@ -384,5 +384,9 @@ def test_homogeneous_stress_under_its_traction_is_static(L, oracle_mod, model, p
     case, u0, P = homogeneous_case(I, oracle_mod, model, "own")
     u, v, Pf = run_gpu(L, case.replace(precision=precision), 200, u0, None)
     scale = np.abs(u0).max()
+    record(f"{precision}/homogeneous_{model}", u=float(np.abs(u - u0).max() / scale),
+           P=float(np.abs(Pf - P.reshape(4)).max() / np.abs(P).max()))
+    # the stored populations of the static state are not exact in reduced
+    # precision: the bar on u is each precision's parity bar
     assert np.abs(u - u0).max() <= tol * scale
-    assert np.abs(Pf - P.reshape(4)).max() <= tol * 10 * np.abs(P).max()
+    assert np.abs(Pf - P.reshape(4)).max() <= tol * 5 * np.abs(P).max()
