@@ -148,6 +148,24 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def fp64_alu_roofline(mlups: float):
+    """FP64 is bound by the FP64 pipe, not HBM: FLOP per node from the
+    committed ncu record (if taken on the current kernel source) against the
+    measured FP64 FMA throughput; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "step_fp64_alu.json")) as f:
+            rec = json.load(f)
+        from paper_2502_00920_gb300 import build as B
+        if rec.get("source_hash") != B.source_hash():
+            return None
+        achieved = rec["flops_per_node"] * mlups * 1e6 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": rec["peak_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / rec["peak_tflops"], "flops_per_node": rec["flops_per_node"],
+                "fp64_pipe_active_ncu": rec["fp64_pipe_active"], "peak_source": "measured FP64 FMA probe"}
+    except Exception:
+        return None
+
+
 def time_precision(L, I, torch, precision, n, steps, warmup, stream, v0dev, uref=None):
     """Time one precision on the roofline lattice; with uref (the FP64 u after
     warmup + steps iterations) also state its error."""
@@ -171,6 +189,8 @@ def time_precision(L, I, torch, precision, n, steps, warmup, stream, v0dev, uref
            "bytes_per_node": bpn, "iterations": warmup + steps}
     if uref is not None:
         out["u_rel_err_vs_fp64"] = float((u - uref).abs().max() / uref.abs().max())
+    if precision == "fp64":
+        out["roofline"] = fp64_alu_roofline(out["mlups"])
     return out, u
 
 

@@ -10,13 +10,11 @@ using V1 = Cfg<P, 32, 8, 8>;
 using V2 = Cfg<P, 64, 8, 4>;
 using V3 = Cfg<P, 32, 32, 8>;
 using V4 = Cfg<P, 32, 16, 8>;
-using V8 = Cfg<P, 32, 16, 16>;
 using M6 = MarchCfg<V4, 8, 128, 2>;
 // 0-3: V0-V3 tiles read from global memory; 4: V4 tiles staged by TMA;
 // 5: V4 tiles, persistent blocks with a two-stage TMA ring; 6: row-marching
-// strips over the V4 tile columns; 7: V3 tiles staged by TMA; 8: V8 tiles
-// (V4 with 512 threads), persistent with a two-stage TMA ring
-constexpr int kVariants = 9;
+// strips over the V4 tile columns; 7: V3 tiles staged by TMA
+constexpr int kVariants = 8;
 
 TileShape shape(int v) {
   switch (v) {
@@ -24,7 +22,6 @@ TileShape shape(int v) {
     case 2: return {V2::TX, V2::TY};
     case 3:
     case 7: return {V3::TX, V3::TY};
-    case 8: return {V8::TX, V8::TY};
     case 4:
     case 5:
     case 6: return {V4::TX, V4::TY};
@@ -38,7 +35,6 @@ const char *name(int v) {
     case 5: return "step_tma2_kernel";
     case 6: return "step_march_kernel";
     case 7: return "step_tma_kernel";
-    case 8: return "step_tma2_kernel";
     default: return "step_interior_kernel";
   }
 }
@@ -52,7 +48,6 @@ cudaError_t step(const Params &p, const StepPtrs &s, int v, cudaStream_t st) {
     case 5: return launch_step_tma2<V4>(p, s, st);
     case 6: return launch_step_march<V4, M6>(p, s, st);
     case 7: return launch_step_tma<V3>(p, s, st);
-    case 8: return launch_step_tma2<V8>(p, s, st);
     default: return launch_step<V0>(p, s, st);
   }
 }
@@ -63,7 +58,6 @@ int kernels_per_step(const Params &p, int v) {
     case 2: return step_kernel_count<V2>(p);
     case 3:
     case 7: return step_kernel_count<V3>(p);
-    case 8: return step_kernel_count<V8>(p);
     case 4:
     case 5:
     case 6: return step_kernel_count<V4>(p);
@@ -74,13 +68,12 @@ int kernels_per_step(const Params &p, int v) {
 bool tma_maps(const Params &p, int v, const void *g, const void *u, void *og, void *ou) {
   if (v == 6) return make_march_maps<V4, M6>(p, g, u, og, ou);
   if (v == 7) return make_tma_maps<V3>(p, g, u, og, ou);
-  if (v == 8) return make_tma_maps<V8>(p, g, u, og, ou);
   if (v != 4 && v != 5) return false;
   return make_tma_maps<V4>(p, g, u, og, ou);
 }
 
 const Launchers kL = {kVariants,
-                      (1 << 4) | (1 << 5) | (1 << 6) | (1 << 7) | (1 << 8),
+                      (1 << 4) | (1 << 5) | (1 << 6) | (1 << 7),
                       5,  // default: the fastest on the 16384^2 roofline lattice
                       shape,
                       name,
