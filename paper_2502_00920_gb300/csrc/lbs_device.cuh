@@ -719,14 +719,15 @@ static __global__ void batch_advance_kernel(BatchLattice *lats, int n) {
 template <class C>
 cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
                               int ne, int *err, cudaStream_t st) {
-  static int blocks = 0;
-  if (!blocks) {
+  // resident blocks of the persistent kernel on this device (computed once;
+  // the initialisation of a function-local static is thread-safe)
+  static const int blocks = [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<C, false>, C::NT, 0);
-    blocks = sms * (per > 0 ? per : 1);
-  }
+    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }();
   if (ni > 0) batch_step_kernel<C, false><<<ni < blocks ? ni : blocks, C::NT, 0, st>>>(lats, interior, ni, err);
   if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, st>>>(lats, edge, ne, err);
   if (nlats > 0) batch_advance_kernel<<<(nlats + 127) / 128, 128, 0, st>>>(lats, nlats);
@@ -1091,14 +1092,15 @@ cudaError_t launch_step_tma2(const Params &P, const StepPtrs &S, cudaStream_t st
   const int ni = a_hi - a_lo, nj = b_hi - b_lo;
   if (ni > 0 && nj > 0) {
     if (!S.tm_g || !S.tm_u) return cudaErrorInvalidValue;
-    static int blocks = 0;
-    if (!blocks) {
+    // resident blocks (computed once, after the shared-memory opt-in that
+    // selecting the variant made; thread-safe initialisation)
+    static const int blocks = [] {
       int dev = 0, sms = 0, per = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_tma2_kernel<C>, C::NT, T2::SMEM);
-      blocks = sms * (per > 0 ? per : 1);
-    }
+      return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    }();
     const int ntiles = ni * nj;
     step_tma2_kernel<C><<<ntiles < blocks ? ntiles : blocks, C::NT, T2::SMEM, st>>>(
         P, S, *(const CUtensorMap *)S.tm_g, *(const CUtensorMap *)S.tm_u, a_lo, b_lo, ni, ntiles);
@@ -1361,15 +1363,16 @@ bool make_tma_maps(const Params &P, const void *g, const void *u, void *out_g, v
   using T = TmaCfg<C>;
   using gs = typename C::gs;
   using R = typename C::real;
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // the driver's tensor-map encoder, looked up once (thread-safe initialisation)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return false;
-    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  }
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }();
+  if (!encode) return false;
   const CUtensorMapDataType gt = sizeof(gs) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                  : sizeof(gs) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
