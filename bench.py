@@ -413,6 +413,7 @@ def suite_tension(args, L, I, O, emit, gpu_run, rel, first_nonfinite_gpu, first_
             emit(config="tension_32x32_nh", precision=prec, iterations=steps, mlups=32 * 32 * steps / dt / 1e6,
                  unstable_gpu=unstable, unstable_oracle=k_nan,
                  u_err=rel(u, ur) if fin and np.isfinite(u).all() else None,
+                 v_err=rel(v, vr) if fin and np.isfinite(v).all() else None,
                  P_err=rel(P, Pr) if fin and np.isfinite(P).all() else None,
                  P11_interior=float(P[8:24, 8:24, 0].mean()) if np.isfinite(P).all() else None)
 
