@@ -390,3 +390,39 @@ def test_homogeneous_stress_under_its_traction_is_static(L, oracle_mod, model, p
     # precision: the bar on u is each precision's parity bar
     assert np.abs(u - u0).max() <= tol * scale
     assert np.abs(Pf - P.reshape(4)).max() <= tol * 5 * np.abs(P).max()
+
+
+def shape_cases():
+    """Degenerate and ragged shapes: lattices three nodes wide (every node on
+    a wall, or a 3-node periodic ring whose halos wrap more than once),
+    lattices smaller than one tile, exact multiples of the tile sizes and one
+    node more, and a material with rho0 != 1 and E != 1."""
+    trac = I.Edge("neumann", "linear_ramp", (0.01, -0.004), 0, 40)
+    mov = I.Edge("dirichlet", "const", (0.002, 0.001))
+    P2 = (I.PERIODIC, I.PERIODIC)
+    return {
+        "3x3_mixed": I.Case("s", 3, 3, 0, model="nh", nu=0.2, edges=(I.CLAMPED, trac, I.FREE, mov)),
+        "3x40_walls": I.Case("s", 3, 40, 0, model="svk", nu=0.1, edges=(I.FREE, I.FREE, I.CLAMPED, trac)),
+        "40x3_walls": I.Case("s", 40, 3, 0, model="nh", nu=0.1, edges=(I.CLAMPED, trac, I.FREE, I.FREE)),
+        "3x7_periodic_x": I.Case("s", 3, 7, 0, model="nh", nu=0.2, edges=P2 + (I.CLAMPED, trac)),
+        "5x5_periodic": I.Case("s", 5, 5, 0, model="svk", nu=0.2, edges=P2 + P2),
+        "17x9_sub_tile": I.Case("s", 17, 9, 0, model="nh", nu=0.25, edges=(I.CLAMPED, trac, I.FREE, I.FREE)),
+        "64x48_tile_multiple": I.Case("s", 64, 48, 0, model="nh", nu=0.2, edges=(I.CLAMPED, trac, I.FREE, I.FREE)),
+        "65x49_one_more": I.Case("s", 65, 49, 0, model="nh", nu=0.2, edges=(I.CLAMPED, trac, I.FREE, I.FREE)),
+        "rho2.5_E3": I.Case("s", 41, 27, 0, model="nh", nu=0.2, E=3.0, rho0=2.5,
+                            edges=(I.CLAMPED, trac, I.FREE, mov)),
+    }
+
+
+@pytest.mark.parametrize("name", list(shape_cases()))
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
+def test_degenerate_and_ragged_shapes_match_oracle(L, oracle_mod, name, precision):
+    case = shape_cases()[name].replace(precision=precision)
+    u0, v0 = rnd(case, amp_u=2e-3, amp_v=4e-3) if case.edges[0].kind == "periodic" else (None, None)
+    u, v, P = run_gpu(L, case, 80, u0, v0)
+    ur, vr, Pr = run_oracle(oracle_mod, case, 80, u0, v0)
+    record(f"{precision}/shape_{name}", u=rel(u, ur), v=rel(v, vr), P=rel(P, Pr))
+    assert np.isfinite(ur).all() and np.abs(ur).max() > 1e-7
+    assert rel(u, ur) <= TOL[precision], rel(u, ur)
+    if precision == "fp64":
+        assert rel(v, vr) <= TOL["fp64"], rel(v, vr)
