@@ -16,6 +16,17 @@
  * Every 1000 iterations (at the next scheduling point) each resident lattice
  * is also checked for non-finite values; one that has some is retired at once
  * as LBS_EUNSTABLE, like a handle whose monitor saw them.
+ *
+ * Preemption (preempt_after_s > 0; no counterpart in the paper).  When the
+ * request at the head of the queue has waited preempt_after_s seconds and its
+ * footprint does not fit, resident lattices are swapped out to make room: those
+ * resident for at least preempt_after_s, the most remaining iterations first,
+ * and only lattices with more remaining iterations than the waiting request.
+ * A swapped-out lattice's state goes to host memory owned by the server
+ * (lbs_save), its device memory is released and it rejoins the queue at the
+ * back; on re-admission it resumes from that state (lbs_load), so its result
+ * is bitwise the one it would have had without the interruption.  Nothing is
+ * swapped out unless the waiting request then fits.
  * Each lattice computes exactly what lbs_step computes for it alone.
  *
  * The server owns its device memory and its results until lbs_result hands
@@ -38,6 +49,7 @@ typedef struct {
   int32_t chunk;         /* iterations between scheduling points (0: 64)               */
   int32_t max_resident;  /* cap on resident lattices (0: none)                          */
   int32_t queue_limit;   /* lbs_submit returns LBS_EBUSY beyond this many queued (0: none) */
+  double preempt_after_s; /* > 0: preemption, below (0: never; < 0: LBS_EINVAL)           */
 } lbs_server_config;
 
 enum { LBS_TICKET_QUEUED = 0, LBS_TICKET_RUNNING = 1, LBS_TICKET_DONE = 2, LBS_TICKET_FAILED = 3 };
@@ -52,6 +64,7 @@ typedef struct {
   double t_admit;      /* admission to the GPU (-1 while queued)                  */
   double t_done;       /* completion (-1 until done or failed)                    */
   size_t device_bytes; /* footprint while resident                                */
+  int64_t swaps;       /* times it was swapped out by preemption                  */
 } lbs_ticket_info;
 
 typedef struct {
@@ -61,6 +74,7 @@ typedef struct {
   size_t bytes_in_use;    /* device bytes of resident lattices                 */
   size_t hbm_budget;
   int64_t launches;       /* kernels launched by the worker                    */
+  int64_t preemptions;    /* lattices swapped out to host memory               */
 } lbs_server_stats;
 
 /* Start a server on the current CUDA device.  Errors: LBS_EINVAL (bad

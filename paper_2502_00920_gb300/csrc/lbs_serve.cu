@@ -34,8 +34,12 @@ struct Req {
   int error = LBS_OK;
   int64_t k = 0;
   double t_submit = 0, t_admit = -1, t_done = -1;
+  double t_queued = 0;    // when it (last) entered the queue
+  double t_resident = 0;  // when it (last) became resident
+  int64_t swaps = 0;      // times it was swapped out to make room
   size_t bytes = 0;
   lbs_handle *h = nullptr;
+  std::vector<unsigned char> ckpt;  // state while swapped out (lbs_save)
   std::vector<double> u, v, P;
 };
 
@@ -117,15 +121,43 @@ bool ensure(T *&ptr, int &cap, int need) {
 // interval as a handle's default monitor)
 constexpr int64_t kCheckEvery = 1000;
 
-// true if the lattice's state holds a non-finite value (brings the handle's
-// iteration and buffer parity up to date with the batch first)
-bool unstable(Req *r) {
+// bring the handle up to date with the batch's advance of the lattice
+void sync_handle(Req *r) {
   lbs_handle *h = r->h;
   h->k = r->k;
   h->parity = (int)(r->k & 1);
   h->kdev_value = -1;
+}
+
+// true if the lattice's state holds a non-finite value (brings the handle's
+// iteration and buffer parity up to date with the batch first)
+bool unstable(Req *r) {
+  sync_handle(r);
   lbs_monitors m;
-  return lbs_monitor(h, &m) == LBS_OK && m.nonfinite > 0;
+  return lbs_monitor(r->h, &m) == LBS_OK && m.nonfinite > 0;
+}
+
+// Swap-out victims for a queued request that does not fit: resident lattices
+// resident for at least `protect` seconds, the most remaining iterations
+// first, each with more remaining iterations than the request, until the
+// request fits the budget; empty if it cannot be made to fit.  Called with the
+// server's lock held.
+std::vector<Req *> pick_victims(lbs_server *s, const std::vector<Req *> &res, const Req *head, double now,
+                                double protect) {
+  std::vector<Req *> cand;
+  for (Req *r : res)
+    if (now - r->t_resident >= protect) cand.push_back(r);
+  std::sort(cand.begin(), cand.end(), [](const Req *a, const Req *b) { return a->nsteps - a->k > b->nsteps - b->k; });
+  std::vector<Req *> out;
+  size_t used = s->used;
+  for (Req *r : cand) {
+    if (used + head->bytes <= s->cfg.hbm_budget) break;
+    if (r->nsteps - r->k <= head->nsteps - head->k) break;
+    out.push_back(r);
+    used -= r->bytes;
+  }
+  if (used + head->bytes > s->cfg.hbm_budget) out.clear();
+  return out;
 }
 
 // one chunk of `n` iterations of every resident lattice: replays of a CUDA
@@ -188,7 +220,7 @@ void run(lbs_server *s) {
                                                            : lbs::launchers_fp16();
   for (;;) {
     // admission: FIFO while the footprint fits
-    std::vector<Req *> admit;
+    std::vector<Req *> admit, victims;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       if (res.empty() && s->queue.empty()) {
@@ -207,18 +239,54 @@ void run(lbs_server *s) {
         s->st.resident += 1;
         admit.push_back(r);
       }
+      // preemption: the queue's head has waited long enough and does not fit
+      const double now = s->now();
+      if (s->cfg.preempt_after_s > 0 && admit.empty() && !s->queue.empty() &&
+          now - s->queue.front()->t_queued >= s->cfg.preempt_after_s)
+        victims = pick_victims(s, res, s->queue.front(), now, s->cfg.preempt_after_s);
     }
+    // swap the victims out: state to host memory, device memory released; they
+    // rejoin the queue at the back and resume from their saved state
+    for (Req *r : victims) {
+      sync_handle(r);
+      r->ckpt.resize(lbs_checkpoint_bytes(r->h));
+      const int rc = lbs_save(r->h, r->ckpt.data(), r->ckpt.size());
+      if (rc) {  // the copy failed: the request ends here
+        r->ckpt.clear();
+        finish(s, r, rc);
+      } else {
+        lbs_destroy(r->h);
+        r->h = nullptr;
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->used -= r->bytes;
+        s->st.resident -= 1;
+        s->st.queued += 1;
+        s->st.preemptions += 1;
+        r->state = LBS_TICKET_QUEUED;
+        r->swaps += 1;
+        r->t_queued = s->now();
+        s->queue.push_back(r);
+      }
+      res.erase(std::find(res.begin(), res.end(), r));
+      dirty = true;
+    }
+    if (!victims.empty()) continue;  // admit into the room just made
     for (Req *r : admit) {
-      const int rc = lbs_create(&r->lat, &r->mat, &r->bcs, &r->h);
+      int rc = lbs_create(&r->lat, &r->mat, &r->bcs, &r->h);
+      if (!rc && !r->ckpt.empty()) rc = lbs_load(r->h, r->ckpt.data(), r->ckpt.size());
       if (rc) {
+        if (r->h) lbs_destroy(r->h);
         r->h = nullptr;
         finish(s, r, rc);
         continue;
       }
+      r->ckpt.clear();
+      r->ckpt.shrink_to_fit();
       lbs_set_monitor_interval(r->h, 0);
       std::lock_guard<std::mutex> lk(s->mu);
       r->state = LBS_TICKET_RUNNING;
-      r->t_admit = s->now();
+      if (r->t_admit < 0) r->t_admit = s->now();
+      r->t_resident = s->now();
       res.push_back(r);
       dirty = true;
     }
@@ -307,7 +375,7 @@ extern "C" {
 
 int lbs_server_create(const lbs_server_config *cfg, lbs_server **out) {
   if (!cfg || !out || cfg->precision < LBS_FP64 || cfg->precision > LBS_FP16S || cfg->chunk < 0 ||
-      cfg->max_resident < 0 || cfg->queue_limit < 0) {
+      cfg->max_resident < 0 || cfg->queue_limit < 0 || !(cfg->preempt_after_s >= 0)) {
     lbs::set_error("bad server configuration");
     return LBS_EINVAL;
   }
@@ -370,6 +438,7 @@ int lbs_submit(lbs_server *s, const lbs_lattice *lat, const lbs_material *mat, c
   }
   r->id = s->next_id++;
   r->t_submit = s->now();
+  r->t_queued = r->t_submit;
   s->tickets[r->id] = r;
   s->queue.push_back(r);
   s->st.submitted += 1;
@@ -395,6 +464,7 @@ int lbs_poll(lbs_server *s, uint64_t ticket, lbs_ticket_info *info) {
   info->t_admit = r->t_admit;
   info->t_done = r->t_done;
   info->device_bytes = r->bytes;
+  info->swaps = r->swaps;
   return LBS_OK;
 }
 

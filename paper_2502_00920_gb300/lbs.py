@@ -111,21 +111,22 @@ SIGNATURES = {
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("precision", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("max_resident", ctypes.c_int32), ("queue_limit", ctypes.c_int32)]
+                ("max_resident", ctypes.c_int32), ("queue_limit", ctypes.c_int32),
+                ("preempt_after_s", ctypes.c_double)]
 
 
 class TicketInfo(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("error", ctypes.c_int32), ("iterations", ctypes.c_int64),
                 ("nsteps", ctypes.c_int64), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("swaps", ctypes.c_int64)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("node_updates", ctypes.c_int64),
                 ("busy_seconds", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("preemptions", ctypes.c_int64)]
 
 
 # include/lbs_serve.h
@@ -417,8 +418,9 @@ class Server:
     """Continuous-batching server (include/lbs_serve.h)."""
 
     def __init__(self, precision: str = "fp32", hbm_budget: int = 0, chunk: int = 64, max_resident: int = 0,
-                 queue_limit: int = 0):
-        cfg = ServerConfig(int(hbm_budget), PRECISION[precision], int(chunk), int(max_resident), int(queue_limit))
+                 queue_limit: int = 0, preempt_after_s: float = 0.0):
+        cfg = ServerConfig(int(hbm_budget), PRECISION[precision], int(chunk), int(max_resident), int(queue_limit),
+                           float(preempt_after_s))
         h = _vp()
         check(lib().lbs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
@@ -438,7 +440,7 @@ class Server:
         check(lib().lbs_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(info)))
         return dict(state=TICKET_STATES[info.state], error=info.error, iterations=info.iterations,
                     nsteps=info.nsteps, nx=info.nx, ny=info.ny, t_submit=info.t_submit, t_admit=info.t_admit,
-                    t_done=info.t_done, device_bytes=info.device_bytes)
+                    t_done=info.t_done, device_bytes=info.device_bytes, swaps=info.swaps)
 
     def wait(self, ticket: int, timeout: float = -1.0):
         check(lib().lbs_wait(self._h, ctypes.c_uint64(ticket), float(timeout)))

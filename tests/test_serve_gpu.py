@@ -134,3 +134,44 @@ def test_failures_reported_per_ticket(L):
         with L.Server(precision="fp32", hbm_budget=1 << 20) as srv:
             srv.submit(I.tension(1024, 1024, 10))
     assert e.value.code == L.ENOMEM
+
+
+def test_preemption_lets_a_short_request_pass_a_long_one(L):
+    """With a budget that holds one lattice, a short request that arrives
+    while a long one runs waits behind it (FIFO) unless preemption is on; with
+    it, the long lattice is swapped out to host memory, the short one runs,
+    and the long one resumes.  Both results equal the same lattices run alone,
+    bitwise.  Clamped edges under a body force keep both bounded."""
+    clamped = (I.CLAMPED,) * 4
+    long = I.Case("long", 1024, 1024, 30000, model="nh", nu=0.3, body=(0.0, -0.01), edges=clamped,
+                  precision="fp32")
+    short = I.Case("short", 1024, 1024, 300, model="svk", nu=0.2, body=(0.01, 0.0), edges=clamped,
+                   precision="fp32")
+    budget = int(1.5 * L.footprint(long))
+
+    def run(preempt):
+        with L.Server(precision="fp32", hbm_budget=budget, chunk=32, preempt_after_s=preempt) as srv:
+            tl = srv.submit(long)
+            time.sleep(0.2)
+            ts = srv.submit(short)
+            srv.drain(600)
+            il, is_, st = srv.poll(tl), srv.poll(ts), srv.stats()
+            rl, rs = srv.result(tl), srv.result(ts)
+        assert rl[3] == L.OK and rs[3] == L.OK
+        assert il["t_admit"] < is_["t_submit"] < il["t_done"]  # the short one arrived while the long one ran
+        return il, is_, st, rl[:3], rs[:3]
+
+    il, is_, st, rl, rs = run(0.05)
+    assert is_["t_done"] < il["t_done"]
+    assert il["swaps"] >= 1 and st["preemptions"] >= 1 and is_["swaps"] == 0
+    for got, case in ((rl, long), (rs, short)):
+        for x, y in zip(got, alone(L, case)):
+            assert np.array_equal(x, y), case.name
+    il, is_, st, _, _ = run(0.0)
+    assert is_["t_done"] > il["t_done"] and st["preemptions"] == 0
+
+
+def test_preemption_setting_is_validated(L):
+    with pytest.raises(L.LbsError) as e:
+        L.Server(precision="fp32", preempt_after_s=-1.0)
+    assert e.value.code == L.EINVAL
