@@ -294,8 +294,9 @@ int lbs_autotune_load(const char *path);
 
 /* Install the device allocator used for handle state (NULL, NULL restores
  * cudaMalloc/cudaFree).  alloc(bytes, stream, ctx) returns a device pointer
- * or NULL; release(ptr, stream, ctx) frees it.  Affects handles created
- * afterwards. */
+ * aligned to 256 bytes, or NULL; release(ptr, stream, ctx) frees it.  A block
+ * that is not so aligned is released again and lbs_create fails with
+ * LBS_ENOMEM.  Affects handles created afterwards. */
 typedef void *(*lbs_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*lbs_free_fn)(void *ptr, void *stream, void *ctx);
 int lbs_set_allocator(lbs_alloc_fn alloc, lbs_free_fn release, void *ctx);

@@ -31,7 +31,17 @@ static Allocator current_allocator() {
 
 static void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t st) {
   if (bytes == 0) bytes = 16;
-  if (a.alloc) return a.alloc(bytes, (void *)st, a.ctx);
+  if (a.alloc) {
+    void *p = a.alloc(bytes, (void *)st, a.ctx);
+    // the kernels make 16-byte vector and tensor-copy accesses from the
+    // buffer's base: refuse a block that is not 256-byte aligned
+    if (p && ((uintptr_t)p & 255u) != 0) {
+      if (a.release) a.release(p, (void *)st, a.ctx);
+      lbs::set_error("the installed allocator returned a block that is not 256-byte aligned");
+      return nullptr;
+    }
+    return p;
+  }
   void *p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();

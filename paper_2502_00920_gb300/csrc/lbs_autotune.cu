@@ -42,7 +42,7 @@ int time_variants(const lbs_lattice *lat, const lbs_material *mat, const lbs_bcs
   lbs_tile_variants(lat->precision, &nvar, nullptr, nullptr);
   rc = lbs_set_graph_chunk(h, 0);
   if (!rc) rc = lbs_set_monitor_interval(h, 0);
-  cudaStream_t st;
+  cudaStream_t st = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!rc && (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
               cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
@@ -84,8 +84,12 @@ int lbs_autotune(const lbs_lattice *lat, const lbs_material *mat, const lbs_bcs 
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
       *best = it->second.variant;
+      // ms has one entry per tile variant of this build; a loaded entry may
+      // carry fewer (unknown entries read 0) or more (ignored)
+      int32_t nvar = 0;
+      lbs_tile_variants(lat->precision, &nvar, nullptr, nullptr);
       if (ms)
-        for (size_t v = 0; v < it->second.ms.size(); ++v) ms[v] = it->second.ms[v];
+        for (int32_t v = 0; v < nvar; ++v) ms[v] = (size_t)v < it->second.ms.size() ? it->second.ms[v] : 0.0f;
       return LBS_OK;
     }
   }
@@ -148,7 +152,7 @@ int lbs_autotune_load(const char *path) {
       char *end = nullptr;
       float x = strtof(p, &end);
       if (end == p) break;
-      e.ms.push_back(x);
+      if ((int32_t)e.ms.size() < nvar) e.ms.push_back(x);
       p = end;
       while (*p == ' ') ++p;
     }
