@@ -69,6 +69,7 @@ class Case:
     seed: int = 0
     init_args: dict = field(default_factory=dict, hash=False, compare=False)
     extrap: str = "own"  # Neumann wall values: "own" (boundary node) | "linear" (two-point)
+    gscale_log2: int = 0  # FP16 storage: stored g = g * 2^gscale_log2 (0: chosen from rho0)
 
     @property
     def spacing(self) -> float:

@@ -426,3 +426,25 @@ def test_degenerate_and_ragged_shapes_match_oracle(L, oracle_mod, name, precisio
     assert rel(u, ur) <= TOL[precision], rel(u, ur)
     if precision == "fp64":
         assert rel(v, vr) <= TOL["fp64"], rel(v, vr)
+
+
+@pytest.mark.parametrize("scale", [0, 6, 12, 16])
+def test_fp16_storage_scale(L, oracle_mod, scale):
+    """FP16 storage keeps g * 2^gscale_log2: any scale that keeps the
+    populations inside half precision's range meets the FP16 bar (0 picks
+    2^12 for rho0 = 1)."""
+    case, steps, _ = CASES()["tension_32_nh"]
+    u, v, P = run_gpu(L, case.replace(precision="fp16s", gscale_log2=scale), steps)
+    ur = run_oracle(oracle_mod, case, steps)[0]
+    assert rel(u, ur) <= TOL["fp16s"], rel(u, ur)
+
+
+def test_fp16_scale_that_overflows_is_reported(L):
+    """2^30 times populations of order 0.1 overflows half precision: the run
+    is reported non-finite (LBS_EUNSTABLE), not returned as a result."""
+    case, steps, _ = CASES()["tension_32_nh"]
+    with L.Simulation(case.replace(precision="fp16s", gscale_log2=30), monitor_interval=10) as s:
+        with pytest.raises(L.LbsError) as e:
+            s.step(steps)
+            s.sync()
+        assert e.value.code == L.EUNSTABLE
