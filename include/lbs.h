@@ -228,6 +228,18 @@ size_t lbs_checkpoint_bytes(const lbs_handle *h);
 int lbs_save(lbs_handle *h, void *buf, size_t bytes);
 int lbs_load(lbs_handle *h, const void *buf, size_t bytes);
 
+/* Self-test of the bounded waits (no counterpart in the paper).  The TMA step
+ * kernels wait on an mbarrier for their tile copies with a bounded number of
+ * polls and report LBS_ETIMEOUT (through lbs_sync) instead of hanging.  This
+ * launches one block that arms an mbarrier for tx_bytes of transfer that is
+ * never issued (tx_bytes = 0: none expected, so the barrier completes at
+ * once) and polls it at most `polls` times with the same helper; *timed_out
+ * receives 1 if the wait ran out, 0 if the barrier completed, and *seconds
+ * (if not NULL) the wall time of the call.  The GPU context stays usable.
+ * Synchronous; allocates a 4-byte flag.  Errors: LBS_EINVAL (tx_bytes >=
+ * 2^20, polls == 0, timed_out NULL), LBS_ECUDA. */
+int lbs_selftest_bounded_wait(uint32_t tx_bytes, uint32_t polls, int32_t *timed_out, double *seconds);
+
 /* The handle's current tile variant (LBS_EINVAL for a null handle). */
 int32_t lbs_variant(const lbs_handle *h);
 

@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall"]
-UNITS = ["lbs_api.cu", "lbs_autotune.cu", "lbs_serve.cu", "lbs_fields_static.cu", "kernels_fp64.cu", "kernels_fp32.cu", "kernels_fp16.cu"]
+UNITS = ["lbs_api.cu", "lbs_autotune.cu", "lbs_serve.cu", "lbs_fields_static.cu", "lbs_selftest.cu", "kernels_fp64.cu",
+         "kernels_fp32.cu", "kernels_fp16.cu"]
 
 
 def nvcc() -> str:

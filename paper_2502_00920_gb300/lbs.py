@@ -95,6 +95,8 @@ SIGNATURES = {
     "lbs_tile_variant_kind": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     "lbs_tile_variant_name": (ctypes.c_char_p, [ctypes.c_int32, ctypes.c_int32]),
     "lbs_variant": (ctypes.c_int32, [_vp]),
+    "lbs_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, _i32p,
+                                                 ctypes.POINTER(ctypes.c_double)]),
     "lbs_checkpoint_bytes": (ctypes.c_size_t, [_vp]),
     "lbs_save": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_size_t]),
     "lbs_load": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_size_t]),
@@ -237,6 +239,14 @@ def tile_variant_kind(precision: str, variant: int) -> str:
     if k < 0:
         check(k)
     return "tma" if k == 1 else "global"
+
+
+def selftest_bounded_wait(tx_bytes: int, polls: int):
+    """(timed_out, seconds) of one bounded wait on a barrier armed for
+    tx_bytes that never arrive (see lbs_selftest_bounded_wait)."""
+    out, sec = ctypes.c_int32(), ctypes.c_double()
+    check(lib().lbs_selftest_bounded_wait(int(tx_bytes), int(polls), ctypes.byref(out), ctypes.byref(sec)))
+    return bool(out.value), sec.value
 
 
 def tile_variant_name(precision: str, variant: int) -> str:

@@ -128,3 +128,15 @@ def test_launch_count_device_bytes_and_cfl_flag(L):
         assert not s.cfl_warning
     with L.Simulation(case(nu=0.3)) as s:
         assert s.cfl_warning  # nu > 1/4: the first-order wall bound c_d <= c is exceeded
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(L):
+    """A wait on a barrier armed for bytes that never arrive ends by its own
+    bound and is reported; the same wait with nothing expected completes; the
+    GPU context then runs a lattice as before."""
+    ref = run(L, case())
+    timed_out, sec = L.selftest_bounded_wait(16, 1 << 14)
+    assert timed_out and sec < 30.0
+    timed_out, _ = L.selftest_bounded_wait(0, 1 << 14)
+    assert not timed_out
+    assert same(run(L, case()), ref)
