@@ -313,7 +313,10 @@ typedef void *(*lbs_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*lbs_free_fn)(void *ptr, void *stream, void *ctx);
 int lbs_set_allocator(lbs_alloc_fn alloc, lbs_free_fn release, void *ctx);
 
+/* Static description of an LBS_* code ("unknown error" for others). */
 const char *lbs_strerror(int code);
+/* Message of the last failure in the calling thread (thread-local; valid
+ * until that thread's next failing call), "" if none. */
 const char *lbs_last_error(void);
 
 #ifdef __cplusplus
