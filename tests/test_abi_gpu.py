@@ -140,3 +140,22 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable(L):
     timed_out, _ = L.selftest_bounded_wait(0, 1 << 14)
     assert not timed_out
     assert same(run(L, case()), ref)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16s", "fp64"])
+def test_switching_variant_and_graph_chunk_mid_run(L, precision):
+    """Tile variant and graph chunk changed between steps (graphs are
+    recaptured, TMA descriptors rebuilt for the current buffers): the result
+    is bitwise that of one uninterrupted run with the defaults."""
+    c = case(precision)
+    ref = run(L, c, steps=200)
+    nvar = len(L.tile_variants(precision))
+    with L.Simulation(c) as s:
+        for v, chunk in [(nvar - 1, 64), (0, 0), (4, 2), (nvar // 2, 128), (1, 64)]:
+            s.set_variant(v % nvar)
+            s.set_graph_chunk(chunk)
+            s.step(40)
+        s.sync()
+        assert s.iteration == 200
+        got = s.fields()
+    assert same(got, ref)
