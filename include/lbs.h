@@ -62,6 +62,14 @@ enum { LBS_PERIODIC = 0, LBS_DIRICHLET = 1, LBS_NEUMANN = 2 };
 /* time shape s(t) of a boundary value amp * s(t); t is the iteration k or the
  * time k dt, per edge (lbs_edge.time_unit) */
 enum { LBS_ITERATIONS = 0, LBS_TIME = 1 };
+/* how a Neumann wall rule carries r, Pi and P + Pi(H) from the boundary node
+ * to the wall a link crosses (Sect. 3.3 asks for values "extrapolated to the
+ * boundary" without saying how) */
+enum {
+  LBS_EXTRAP_OWN = 0,   /* the boundary node's own values (zeroth order)      */
+  LBS_EXTRAP_LINEAR = 1 /* two-point: v + (v - v_in) / 2 for each crossed wall,
+                           v_in at the next node inwards along its normal     */
+};
 enum {
   LBS_CONST = 0,       /* 1                                                  */
   LBS_LINEAR_RAMP = 1, /* clamp((k - t0) / (t1 - t0), 0, 1)                  */
@@ -80,6 +88,8 @@ typedef struct {
   double tau;          /* BGK relaxation time in units of dt (> 0.5)         */
   int32_t precision;   /* LBS_FP64 | LBS_FP32 | LBS_FP16S                    */
   int32_t gscale_log2; /* LBS_FP16S: stored g = g * 2^gscale_log2; 0 = auto  */
+  int32_t wall_extrap; /* LBS_EXTRAP_OWN (0) | LBS_EXTRAP_LINEAR; LINEAR keeps
+                          a second layer of the boundary side array           */
 } lbs_lattice;
 
 typedef struct {

@@ -92,6 +92,8 @@ static int validate(const lbs_lattice *lat, const lbs_material *mat, const lbs_b
   if (!(lat->dx > 0.0)) return fail(LBS_EINVAL, "dx must be positive");
   if (lat->precision < LBS_FP64 || lat->precision > LBS_FP16S) return fail(LBS_EINVAL, "unknown precision");
   if (lat->gscale_log2 < -30 || lat->gscale_log2 > 30) return fail(LBS_EINVAL, "gscale_log2 out of range");
+  if (lat->wall_extrap != LBS_EXTRAP_OWN && lat->wall_extrap != LBS_EXTRAP_LINEAR)
+    return fail(LBS_EINVAL, "unknown wall extrapolation");
   if (mat->model < LBS_SVK || mat->model > LBS_LE) return fail(LBS_EINVAL, "unknown material model");
   if (!(mat->E > 0.0) || !(mat->rho0 > 0.0)) return fail(LBS_EINVAL, "E and rho0 must be positive");
   if (!(mat->nu > -1.0 && mat->nu < 0.5)) return fail(LBS_EINVAL, "nu must lie in (-1, 0.5)");
@@ -146,6 +148,7 @@ static Params make_params(const lbs_lattice *lat, const lbs_material *mat, const
   p.blen = lat->nx > lat->ny ? lat->nx : lat->ny;
   p.model = mat->model;
   p.gshift = auto_gshift(lat, mat);
+  p.extrap = lat->wall_extrap == LBS_EXTRAP_LINEAR;
   lbs_bcs zero;
   memset(&zero, 0, sizeof(zero));
   for (int e = 0; e < 4; ++e) zero.edge[e].type = LBS_NEUMANN;
@@ -196,7 +199,7 @@ static Sizes sizes_of(const Params &p, const Launchers &L) {
   Sizes s;
   s.g = (size_t)9 * p.ny * p.pitch * L.g_elem;
   s.u = (size_t)p.ny * p.pitch * L.u_elem;
-  s.b = (size_t)4 * p.blen * 4 * L.b_elem;
+  s.b = (size_t)(p.extrap ? 2 : 1) * 4 * p.blen * 4 * L.b_elem;
   s.mon = (size_t)monitor_blocks(p) * 5 * sizeof(double) + 8 * sizeof(double) + 3 * sizeof(int64_t);
   return s;
 }
@@ -349,7 +352,9 @@ int lbs_params(const lbs_lattice *lat, const lbs_material *mat, double out[5]) {
 }
 
 size_t lbs_footprint(const lbs_lattice *lat) {
-  if (!lat || lat->nx < 3 || lat->ny < 3 || lat->precision < LBS_FP64 || lat->precision > LBS_FP16S) return 0;
+  if (!lat || lat->nx < 3 || lat->ny < 3 || lat->precision < LBS_FP64 || lat->precision > LBS_FP16S ||
+      (lat->wall_extrap != LBS_EXTRAP_OWN && lat->wall_extrap != LBS_EXTRAP_LINEAR))
+    return 0;
   lbs_material m = {LBS_NH, 1.0, 0.3, 1.0, {0.0, 0.0}};
   Params p = make_params(lat, &m, nullptr);
   Sizes s = sizes_of(p, launchers_for(lat->precision));

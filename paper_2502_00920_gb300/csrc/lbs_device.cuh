@@ -227,9 +227,13 @@ __device__ inline void edge_value(const Params &P, int e, int64_t k, double out[
 // crossing two walls is Dirichlet if either wall is (mean j* if both), else
 // its Pi* takes Pi*_xx from the x wall, Pi*_yy from the y wall and the mean of
 // the two shear entries.
-template <class R>
-__device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t k, const R g0[9], unsigned mask,
-                           R f[9], R gsc) {
+// Under two-point extrapolation (P.extrap) each of these node values v is
+// carried to the wall(s) the link crosses as v + (v - v_in)/2 per crossed
+// wall, v_in the value at the next node inwards along that wall's normal: r
+// and Pi from that node's own g, N from the side array's second layer.
+template <class R, class G, bool LIN>
+__device__ void wall_rules(const Params &P, const R *bnd, const G *g, int x, int y, int64_t k, const R g0[9],
+                           unsigned mask, R f[9], R gsc) {
   int xw = -1, yw = -1;
   if (!P.per_x) xw = (x == 0) ? kLeft : ((x == P.nx - 1) ? kRight : -1);
   if (!P.per_y) yw = (y == 0) ? kBottom : ((y == P.ny - 1) ? kTop : -1);
@@ -266,6 +270,42 @@ __device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t 
     Ayy_y = (Nn[3] - s * (R)T[1]) * ics2;
     axy_y = (Nn[1] - s * (R)T[0]) * ics2;
   }
+  // two-point extrapolation: half the differences own - inner of r, A and N
+  // for the x wall (dX, nX) and the y wall (dY, nY) the node sits on
+  R dX[4] = {0, 0, 0, 0}, dY[4] = {0, 0, 0, 0}, nX[4] = {0, 0, 0, 0}, nY[4] = {0, 0, 0, 0};
+  if constexpr (LIN) {
+    const size_t plane = (size_t)P.ny * P.pitch;
+    const R *inner = bnd + (size_t)4 * P.blen * 4;  // second layer of the side array
+    const R own[4] = {r, Axx_o, Axy_o, Ayy_o};
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int e = w == 0 ? xw : yw;
+      if (e < 0) continue;
+      const int xi = w == 0 ? (e == kLeft ? x + 1 : x - 1) : x;
+      const int yi = w == 0 ? y : (e == kBottom ? y + 1 : y - 1);
+      const size_t idx = (size_t)yi * P.pitch + xi;
+      R ri = 0, ixx = 0, ixy = 0, iyy = 0;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const R v = gload(g, q * plane + idx, R(1));
+        ri += v;
+        ixx += R(ex(q) * ex(q)) * v;
+        ixy += R(ex(q) * ey(q)) * v;
+        iyy += R(ey(q) * ey(q)) * v;
+      }
+      const R in[4] = {ri, R(3) * ixx, R(3) * ixy, R(3) * iyy};
+      const int pos = w == 0 ? y : x;
+      const R *N0 = bnd + ((size_t)e * P.blen + pos) * 4;
+      const R *N1 = inner + ((size_t)e * P.blen + pos) * 4;
+      R *d = w == 0 ? dX : dY;
+      R *n = w == 0 ? nX : nY;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        d[m] = R(0.5) * (own[m] - in[m]);
+        n[m] = R(0.5) * (N0[m] - N1[m]) * ics2;
+      }
+    }
+  }
   const R cj = (R)(P.c * P.inv_cs2) * gsc;
 #pragma unroll
   for (int q = 1; q < 9; ++q) {
@@ -287,7 +327,7 @@ __device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t 
         edge_value(P, dxw ? xw : yw, k, js);
       }
       f[q] = g0[qb] + R(2) * wq<R>(q) * cj * (R(ex(q)) * (R)js[0] + R(ey(q)) * (R)js[1]);
-    } else {
+    } else if constexpr (!LIN) {
       // Pi* of the wall(s) this link crosses
       const R Axx = ox ? Axx_x : Axx_o;
       const R Ayy = oy ? Ayy_y : Ayy_o;
@@ -295,6 +335,20 @@ __device__ void wall_rules(const Params &P, const R *bnd, int x, int y, int64_t 
       const R e2 = R(ex(q) * ex(q) + ey(q) * ey(q));
       const R eAe = R(ex(q) * ex(q)) * Axx + R(2 * ex(q) * ey(q)) * Axy + R(ey(q) * ey(q)) * Ayy;
       f[q] = -g0[qb] + wq<R>(q) * (R(4) * r - R(3) * r * e2 + R(3) * eAe - (Axx + Ayy));
+    } else {
+      // the same with the values extrapolated across the crossed walls only
+      const R ax = ox ? R(1) : R(0), ay = oy ? R(1) : R(0);
+      auto e = [&](int m, const R *a, const R *b) { return ax * a[m] + ay * b[m]; };
+      const R rw = r + e(0, dX, dY);
+      const R Axx_e = Axx_o + e(1, dX, dY), Axy_e = Axy_o + e(2, dX, dY), Ayy_e = Ayy_o + e(3, dX, dY);
+      const R axx_x = Axx_x + e(0, nX, nY), axy_xe = axy_x + e(2, nX, nY);
+      const R ayy_y = Ayy_y + e(3, nX, nY), axy_ye = axy_y + e(1, nX, nY);
+      const R Axx = ox ? axx_x : Axx_e;
+      const R Ayy = oy ? ayy_y : Ayy_e;
+      const R Axy = (ox && oy) ? R(0.5) * (axy_xe + axy_ye) : (ox ? axy_xe : (oy ? axy_ye : Axy_e));
+      const R e2 = R(ex(q) * ex(q) + ey(q) * ey(q));
+      const R eAe = R(ex(q) * ex(q)) * Axx + R(2 * ex(q) * ey(q)) * Axy + R(ey(q) * ey(q)) * Ayy;
+      f[q] = -g0[qb] + wq<R>(q) * (R(4) * rw - R(3) * rw * e2 + R(3) * eAe - (Axx + Ayy));
     }
   }
 }
@@ -395,8 +449,9 @@ __device__ __forceinline__ bool locate(const Params &P, int &x, int &y) {
 
 // Stream into node (x, y) (already wrapped into the lattice) and return the
 // first moments sum_q e_q g_q (own node, post-collision at k) and
-// sum_q e_q f_q (streamed, at k + 1).  EDGE: wrap, walls and boundary rules.
-template <class Pr, bool EDGE>
+// sum_q e_q f_q (streamed, at k + 1).  EDGE: wrap, walls and boundary rules;
+// LIN: the two-point wall extrapolation (lattices with P.extrap set).
+template <class Pr, bool EDGE, bool LIN>
 __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *__restrict__ g, const typename Pr::real *bnd,
                                        int x, int y, int64_t k, typename Pr::real inv, typename Pr::real f[9],
                                        typename Pr::real &gx, typename Pr::real &gy, typename Pr::real gsc) {
@@ -432,7 +487,7 @@ __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *_
         f[q] = gload(g, q * plane + (size_t)sy * P.pitch + sx, inv);
       }
     }
-    if (mask) wall_rules<R>(P, bnd, x, y, k, g0, mask, f, gsc);
+    if (mask) wall_rules<R, typename Pr::gs, LIN>(P, bnd, g, x, y, k, g0, mask, f, gsc);
   }
   gx = (g0[1] - g0[3]) + (g0[5] - g0[6]) + (g0[8] - g0[7]);
   gy = (g0[2] - g0[4]) + (g0[5] - g0[8]) + (g0[6] - g0[7]);
@@ -452,6 +507,25 @@ __device__ __forceinline__ void store_wall_n(const Params &P, R *bnd, int x, int
   if (!P.per_y && (y == 0 || y == P.ny - 1)) {
     R *d = bnd + ((size_t)(y == 0 ? kBottom : kTop) * P.blen + x) * 4;
     for (int m = 0; m < 4; ++m) d[m] = N[m];
+  }
+}
+
+// under two-point extrapolation: store N of node (x, y) into the side array's
+// second layer for each wall it lies one step inwards from
+template <class R>
+__device__ __forceinline__ void store_inner_n(const Params &P, R *bnd, int x, int y, const R N[4]) {
+  R *inner = bnd + (size_t)4 * P.blen * 4;
+  auto put = [&](int e, int pos) {
+    R *d = inner + ((size_t)e * P.blen + pos) * 4;
+    for (int m = 0; m < 4; ++m) d[m] = N[m];
+  };
+  if (!P.per_x) {
+    if (x == 1) put(kLeft, y);
+    if (x == P.nx - 2) put(kRight, y);
+  }
+  if (!P.per_y) {
+    if (y == 1) put(kBottom, x);
+    if (y == P.ny - 2) put(kTop, x);
   }
 }
 
@@ -506,8 +580,9 @@ struct Fd {
 };
 
 // phase 2: N over R1 from u in shared memory; N of own-tile wall nodes goes
-// to the side array
-template <class C, bool EDGE>
+// to the side array (and, with LIN on a lattice with P.extrap set, N of the
+// nodes one step inwards to its second layer)
+template <class C, bool EDGE, bool LIN = false>
 __device__ __forceinline__ void phase_n(typename C::Smem &sm, const Params &P, int x0, int y0, typename C::real *bnd_out) {
   using R = typename C::real;
   const R lam = (R)P.lam, mu = (R)P.mu, idx_ = (R)P.inv_dx;
@@ -521,13 +596,15 @@ __device__ __forceinline__ void phase_n(typename C::Smem &sm, const Params &P, i
 #pragma unroll
     for (int m = 0; m < 4; ++m) sm.n[m][ry][rx] = N[m];
     if (EDGE && bnd_out && rx >= 1 && rx <= C::TX && ry >= 1 && ry <= C::TY && x0 - 1 + rx < P.nx &&
-        y0 - 1 + ry < P.ny && on_wall(P, gx, gy))
-      store_wall_n<R>(P, bnd_out, gx, gy, N);
+        y0 - 1 + ry < P.ny) {
+      if (on_wall(P, gx, gy)) store_wall_n<R>(P, bnd_out, gx, gy, N);
+      if (LIN && P.extrap) store_inner_n<R>(P, bnd_out, gx, gy, N);
+    }
   }
 }
 
 // The fused iteration on one tile.
-template <class C, bool EDGE>
+template <class C, bool EDGE, bool LIN = false>
 __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, int x0, int y0) {
   using Pr_real = typename C::real;
   using R = Pr_real;
@@ -556,7 +633,7 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     int x = x0 + lx, y = y0 + ly;
     if (EDGE && !locate(P, x, y)) continue;
     R gxm, gym;
-    gather<typename C::PrT, EDGE>(P, g, bnd, x, y, k, inv, f[i], gxm, gym, scl);
+    gather<typename C::PrT, EDGE, LIN>(P, g, bnd, x, y, k, inv, f[i], gxm, gym, scl);
     const R fx = (f[i][1] - f[i][3]) + (f[i][5] - f[i][6]) + (f[i][8] - f[i][7]);
     const R fy = (f[i][2] - f[i][4]) + (f[i][5] - f[i][8]) + (f[i][6] - f[i][7]);
     sm.u[ly + 2][lx + 2] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
@@ -568,13 +645,13 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     int x = x0 - 2 + rx, y = y0 - 2 + ry;
     if (EDGE && !locate(P, x, y)) continue;
     R ff[9], gxm, gym;
-    gather<typename C::PrT, EDGE>(P, g, bnd, x, y, k, inv, ff, gxm, gym, scl);
+    gather<typename C::PrT, EDGE, LIN>(P, g, bnd, x, y, k, inv, ff, gxm, gym, scl);
     const R fx = (ff[1] - ff[3]) + (ff[5] - ff[6]) + (ff[8] - ff[7]);
     const R fy = (ff[2] - ff[4]) + (ff[5] - ff[8]) + (ff[6] - ff[7]);
     sm.u[ry][rx] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
   }
   __syncthreads();
-  phase_n<C, EDGE>(sm, P, x0, y0, (R *)S.b_out);
+  phase_n<C, EDGE, LIN>(sm, P, x0, y0, (R *)S.b_out);
   __syncthreads();
   // phase 3: source, collision, store
   const size_t plane = (size_t)P.ny * P.pitch;
@@ -630,12 +707,22 @@ __host__ __device__ inline void edge_tile(int e, int ntx, int a_lo, int a_hi, in
   b = b_hi + e / ntx;
 }
 
-template <class C>
+template <class C, bool LIN>
 __global__ void __launch_bounds__(C::NT) step_edge_kernel(const Params P, const StepPtrs S, int ntx, int a_lo, int a_hi,
                                                           int b_lo, int b_hi) {
   int a, b;
   edge_tile(blockIdx.x, ntx, a_lo, a_hi, b_lo, b_hi, a, b);
-  step_tile<C, true>(P, S, a * C::TX, b * C::TY);
+  step_tile<C, true, LIN>(P, S, a * C::TX, b * C::TY);
+}
+
+// the frame tiles of one iteration; the two-point wall extrapolation has its
+// own instantiation so that the default frame kernel keeps its registers
+template <class C>
+void launch_edge(const Params &P, const StepPtrs &S, int nedge, int ntx, int a_lo, int a_hi, int b_lo, int b_hi,
+                 cudaStream_t st) {
+  if (nedge <= 0) return;
+  if (P.extrap) step_edge_kernel<C, true><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+  else step_edge_kernel<C, false><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
 }
 
 // interior tile range [a_lo, a_hi) x [b_lo, b_hi): R2 of the tile and the
@@ -667,7 +754,7 @@ cudaError_t launch_step(const Params &P, const StepPtrs &S, cudaStream_t st) {
   const int ni = a_hi - a_lo, nj = b_hi - b_lo;
   if (ni > 0 && nj > 0) step_interior_kernel<C><<<dim3(ni, nj), C::NT, 0, st>>>(P, S, a_lo, b_lo);
   const int nedge = ntx * nty - ni * nj;
-  if (nedge > 0) step_edge_kernel<C><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+  launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
   return cudaGetLastError();
 }
 
@@ -676,7 +763,7 @@ cudaError_t launch_step(const Params &P, const StepPtrs &S, cudaStream_t st) {
 // different sizes: block i takes tiles i, i + grid, ...  Each tile runs the
 // same step_tile code as the single-lattice kernels, on its lattice's buffers
 // chosen by the parity of that lattice's iteration counter.
-template <class C, bool EDGE>
+template <class C, bool EDGE, bool LIN = false>
 __global__ void __launch_bounds__(C::NT) batch_step_kernel(const BatchLattice *lats, const BatchTile *tiles, int ntiles,
                                                            int *err) {
   __shared__ Params sP;
@@ -705,7 +792,7 @@ __global__ void __launch_bounds__(C::NT) batch_step_kernel(const BatchLattice *l
     __syncthreads();
     if (!skip) {
       const BatchTile T = tiles[t];
-      step_tile<C, EDGE>(sP, sS, T.a * C::TX, T.b * C::TY);
+      step_tile<C, EDGE, LIN>(sP, sS, T.a * C::TX, T.b * C::TY);
     }
     __syncthreads();  // the next tile reuses the shared memory
   }
@@ -718,7 +805,7 @@ static __global__ void batch_advance_kernel(BatchLattice *lats, int n) {
 
 template <class C>
 cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
-                              int ne, int *err, cudaStream_t st) {
+                              int ne, bool lin, int *err, cudaStream_t st) {
   // resident blocks of the persistent kernel on this device (computed once;
   // the initialisation of a function-local static is thread-safe)
   static const int blocks = [] {
@@ -729,7 +816,8 @@ cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *in
     return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }();
   if (ni > 0) batch_step_kernel<C, false><<<ni < blocks ? ni : blocks, C::NT, 0, st>>>(lats, interior, ni, err);
-  if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, st>>>(lats, edge, ne, err);
+  if (ne > 0 && lin) batch_step_kernel<C, true, true><<<ne < blocks ? ne : blocks, C::NT, 0, st>>>(lats, edge, ne, err);
+  else if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, st>>>(lats, edge, ne, err);
   if (nlats > 0) batch_advance_kernel<<<(nlats + 127) / 128, 128, 0, st>>>(lats, nlats);
   return cudaGetLastError();
 }
@@ -924,7 +1012,7 @@ cudaError_t launch_step_tma(const Params &P, const StepPtrs &S, cudaStream_t st)
                                                                *(const CUtensorMap *)S.tm_u, a_lo, b_lo);
   }
   const int nedge = ntx * nty - ni * nj;
-  if (nedge > 0) step_edge_kernel<C><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+  launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
   return cudaGetLastError();
 }
 
@@ -1106,7 +1194,7 @@ cudaError_t launch_step_tma2(const Params &P, const StepPtrs &S, cudaStream_t st
         P, S, *(const CUtensorMap *)S.tm_g, *(const CUtensorMap *)S.tm_u, a_lo, b_lo, ni, ntiles);
   }
   const int nedge = ntx * nty - ni * nj;
-  if (nedge > 0) step_edge_kernel<C><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+  launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
   return cudaGetLastError();
 }
 
@@ -1319,7 +1407,7 @@ cudaError_t launch_step_march(const Params &P, const StepPtrs &S, cudaStream_t s
                                                                *(const CUtensorMap *)S.tm_u, a_lo, ni, y_first, y_last);
   }
   const int nedge = ntx * nty - ni * nj;
-  if (nedge > 0) step_edge_kernel<C><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+  launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
   return cudaGetLastError();
 }
 
@@ -1430,7 +1518,7 @@ __global__ void __launch_bounds__(C::NT) init_kernel(const Params P, typename C:
   const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
   load_r2_from_double<C>(sm, P, u0, x0, y0);
   __syncthreads();
-  phase_n<C, true>(sm, P, x0, y0, bnd);
+  phase_n<C, true, true>(sm, P, x0, y0, bnd);
   __syncthreads();
   const size_t plane = (size_t)P.ny * P.pitch;
   const R idx_ = (R)P.inv_dx, scl = gscale<typename C::gs, R>(P);

@@ -21,6 +21,7 @@ struct Params {
   int blen;           // entries per edge of the boundary side array
   int model;
   int gshift;         // FP16S: stored g = g * 2^gshift
+  int extrap;         // Neumann wall values: 0 the boundary node's own, 1 two-point linear
   int etype[4], eshape[4], eunit[4];
   double eamp[4][2], et0[4], et1[4], es[4];
   double mu, lam, rho0, cs, c, dt, dx, tau;
@@ -35,7 +36,9 @@ struct Params {
 
 // Device pointers of one lattice for one step: in/out buffers of the
 // distributions g (9 planes of ny*pitch), the displacement u (one record per
-// node) and the boundary side array (4 edges x blen x 4 entries of N = P + Pi(H)).
+// node) and the boundary side array (4 edges x blen x 4 entries of N = P + Pi(H)
+// at the wall nodes; under two-point extrapolation a second such layer holds N
+// at the nodes one step inwards from each wall).
 struct StepPtrs {
   const void *g_in;
   void *g_out;
@@ -90,9 +93,10 @@ struct Launchers {
   cudaError_t (*probe)(const Params &p, const void *u, const int32_t *idx, int n, double *out, cudaStream_t st);
   // one iteration of every unfinished lattice of a batch: interior tiles,
   // frame tiles, then the per-lattice counters (tile shape of the default
-  // global-memory variant, batch_tile())
+  // global-memory variant, batch_tile()); `lin`: some lattice of the batch
+  // takes two-point wall extrapolation (its frame tiles need that kernel)
   cudaError_t (*batch_step)(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
-                            int ne, int *err, cudaStream_t st);
+                            int ne, bool lin, int *err, cudaStream_t st);
   TileShape batch_tile;
   size_t g_elem, u_elem, b_elem;  // bytes per stored g value, per u record, per boundary entry
 };

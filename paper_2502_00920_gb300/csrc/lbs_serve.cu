@@ -175,10 +175,12 @@ struct ChunkGraph {
   }
 };
 
-cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int nres, int ni, int ne, int64_t n, ChunkGraph &G) {
+cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int nres, int ni, int ne, bool lin, int64_t n,
+                      ChunkGraph &G) {
   auto direct = [&]() -> cudaError_t {
     for (int64_t it = 0; it < n; ++it) {
-      const cudaError_t e = L.batch_step(s->d_lats, nres, s->d_tiles, ni, s->d_tiles + ni, ne, s->d_err, s->stream);
+      const cudaError_t e =
+          L.batch_step(s->d_lats, nres, s->d_tiles, ni, s->d_tiles + ni, ne, lin, s->d_err, s->stream);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -214,6 +216,7 @@ void run(lbs_server *s) {
   std::vector<BatchLattice> hl;
   std::vector<BatchTile> ht;
   int ni = 0, ne = 0;
+  bool lin = false;  // a resident lattice takes two-point wall extrapolation
   bool dirty = true;
   const lbs::Launchers &L = s->cfg.precision == LBS_FP64   ? lbs::launchers_fp64()
                             : s->cfg.precision == LBS_FP32 ? lbs::launchers_fp32()
@@ -298,10 +301,12 @@ void run(lbs_server *s) {
       ht.clear();
       std::vector<BatchTile> edge;
       const int TX = L.batch_tile.tx, TY = L.batch_tile.ty;
+      lin = false;
       for (size_t i = 0; i < res.size(); ++i) {
         lbs_handle *h = res[i]->h;
         BatchLattice &B = hl[i];
         B.P = h->P;
+        lin = lin || h->P.extrap;
         for (int p = 0; p < 2; ++p) {
           B.g[p] = h->g[p];
           B.u[p] = h->u[p];
@@ -337,7 +342,7 @@ void run(lbs_server *s) {
     chunk = std::min(chunk, longest);
     const double tb = s->now();
     const int64_t launched = chunk * ((ni > 0) + (ne > 0) + 1);
-    cudaError_t e = run_chunk(s, L, (int)res.size(), ni, ne, chunk, graph);
+    cudaError_t e = run_chunk(s, L, (int)res.size(), ni, ne, lin, chunk, graph);
     const cudaError_t es = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = es;
     {

@@ -26,6 +26,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3
 PRECISION = {"fp64": 0, "fp32": 1, "fp16s": 2}
 MODEL = {"svk": 0, "nh": 1, "le": 2}
 KIND = {"periodic": 0, "dirichlet": 1, "neumann": 2}
+EXTRAP = {"own": 0, "linear": 1}  # LBS_EXTRAP_OWN, LBS_EXTRAP_LINEAR
 UNIT = {"steps": 0, "time": 1}
 SHAPE = {"const": 0, "linear_ramp": 1, "sin2_ramp": 2, "half_sine": 3, "ricker": 4, "disp_ramp": 5}
 
@@ -38,7 +39,7 @@ class LbsError(RuntimeError):
 
 class Lattice(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_double), ("tau", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("gscale_log2", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("gscale_log2", ctypes.c_int32), ("wall_extrap", ctypes.c_int32)]
 
 
 class Material(ctypes.Structure):
@@ -174,11 +175,9 @@ def _ptr(a: np.ndarray):
 
 def structs(case):
     """(Lattice, Material, Bcs) of a Case."""
-    if getattr(case, "extrap", "own") != "own":
-        raise ValueError("liblbs carries the boundary node's own values to the wall; the two-point linear "
-                         "extrapolation exists in the oracle only")
     lat = Lattice(int(case.nx), int(case.ny), float(case.dx if case.dx is not None else 1.0 / case.ny),
-                  float(case.tau), PRECISION[case.precision], int(getattr(case, "gscale_log2", 0) or 0))
+                  float(case.tau), PRECISION[case.precision], int(getattr(case, "gscale_log2", 0) or 0),
+                  EXTRAP[getattr(case, "extrap", "own")])
     mat = Material(MODEL[case.model], float(case.E), float(case.nu), float(case.rho0),
                    (ctypes.c_double * 2)(float(case.body[0]), float(case.body[1])))
     bcs = Bcs()

@@ -80,6 +80,22 @@ def test_footprint_accounts_for_state(L):
     assert L.footprint(small.replace(precision="fp64")) > fp > L.footprint(small.replace(precision="fp16s"))
 
 
+def test_linear_wall_extrapolation_adds_a_second_side_array_layer(L):
+    """LBS_EXTRAP_LINEAR keeps N at the nodes one step inwards from each wall:
+    one more layer of 4 edges x max(nx, ny) x 4 entries in each of the two
+    state buffers; an unknown mode is rejected before any device work."""
+    import ctypes
+    small = I.Case("f", 64, 32, 0, precision="fp32")
+    assert L.footprint(small.replace(extrap="linear")) - L.footprint(small) == 2 * 4 * 64 * 4 * 4
+    assert L.footprint(small.replace(extrap="linear", precision="fp64")) - L.footprint(
+        small.replace(precision="fp64")) == 2 * 4 * 64 * 4 * 8
+    lat, mat, bcs = L.structs(small)
+    lat.wall_extrap = 7
+    h = ctypes.c_void_p()
+    assert L.lib().lbs_create(ctypes.byref(lat), ctypes.byref(mat), ctypes.byref(bcs), ctypes.byref(h)) == L.EINVAL
+    assert L.lib().lbs_footprint(ctypes.byref(lat)) == 0
+
+
 def test_invalid_configurations_are_rejected(L):
     bad = [I.Case("b", 2, 8, 0), I.Case("b", 8, 8, 0, tau=0.5), I.Case("b", 8, 8, 0, nu=0.5),
            I.Case("b", 8, 8, 0, edges=(I.PERIODIC, I.FREE, I.FREE, I.FREE)),

@@ -20,15 +20,18 @@ def L():
     return lbs
 
 
-def case(precision):
+def case(precision, extrap="own"):
     trac = I.Edge("neumann", "linear_ramp", (0.01, -0.005), 0, 120)
     return I.Case("ck", 70, 45, 0, model="nh", nu=0.2, edges=(I.CLAMPED, trac, I.FREE, I.FREE),
-                  precision=precision)
+                  precision=precision, extrap=extrap)
 
 
+@pytest.mark.parametrize("extrap", ["own", "linear"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
-def test_resume_is_bitwise(L, precision):
-    c = case(precision)
+def test_resume_is_bitwise(L, precision, extrap):
+    """With the linear wall reading the checkpoint carries both layers of the
+    boundary side array."""
+    c = case(precision, extrap)
     with L.Simulation(c) as a:
         a.step(130)  # two graph chunks and two direct iterations: buffers swapped
         ck = a.save()
@@ -55,7 +58,7 @@ def test_load_refuses_other_configurations(L):
     with L.Simulation(case("fp32")) as a:
         a.step(10)
         ck = a.save()
-    for other in (case("fp32").replace(nx=71), case("fp64"), case("fp32").replace(nu=0.25)):
+    for other in (case("fp32").replace(nx=71), case("fp64"), case("fp32").replace(nu=0.25), case("fp32", "linear")):
         with L.Simulation(other) as b:
             with pytest.raises(L.LbsError) as e:
                 b.load(ck)

@@ -1,0 +1,156 @@
+"""Two-point linear wall extrapolation on the GPU (LBS_EXTRAP_LINEAR): the
+other reading of the Neumann rule's values "extrapolated to the boundary"
+(Sect. 3.3).  r, Pi and P + Pi(H) are carried from the boundary node to each
+crossed wall as v + (v - v_in)/2.  Checked against the oracle's
+ORA_EXTRAP_LINEAR, whose pins (the homogeneous static block) hold for both
+readings, over the same cases as the default reading: walls of every kind,
+Neumann-Neumann and mixed corners, one periodic axis, lattices three nodes
+wide (the inner nodes of opposite walls coincide) and ragged tiles.  The
+histories stop before the reading's own instability sets in; where it does
+set in (the bending wave), both codes find the same first non-finite
+iteration."""
+import numpy as np
+import pytest
+
+from paper_2502_00920_gb300 import inputs as I
+from test_parity_gpu import CASES, TOL, record, rel, rnd, run_gpu, run_oracle, shape_cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2502_00920_gb300 import build
+    build.build()
+    from paper_2502_00920_gb300 import lbs
+    return lbs
+
+
+def lin_cases():
+    """(case, iterations, initial state) with the linear reading.  The 32 x 32
+    tension case runs 200 iterations: under this reading it goes non-finite
+    at iteration 372 (oracle)."""
+    out = {}
+    for name, steps in (("tension_32_nh", 200), ("corners_nn_45x33", 150), ("mixed_37x29", 200),
+                        ("periodic_x_walls_y_64x40", 200), ("cantilever_256x32", 300), ("walls_150x100_nh", 200)):
+        case, _, random_init = CASES()[name]
+        out[name] = (case.replace(extrap="linear"), steps, random_init)
+    for name in ("3x3_mixed", "3x40_walls", "40x3_walls", "17x9_sub_tile", "65x49_one_more", "rho2.5_E3"):
+        out["shape_" + name] = (shape_cases()[name].replace(extrap="linear"), 80, False)
+    return out
+
+
+def initial(case, random_init):
+    return rnd(case) if random_init else (None, None)
+
+
+@pytest.mark.parametrize("name", list(lin_cases()))
+def test_fp64_linear_extrapolation_matches_oracle(L, oracle_mod, name):
+    case, steps, random_init = lin_cases()[name]
+    case = case.replace(precision="fp64")
+    u0, v0 = initial(case, random_init)
+    u, v, P = run_gpu(L, case, steps, u0, v0)
+    ur, vr, Pr = run_oracle(oracle_mod, case, steps, u0, v0)
+    record(f"fp64/linear_{name}", u=rel(u, ur), v=rel(v, vr), P=rel(P, Pr))
+    assert np.isfinite(ur).all() and np.abs(ur).max() > 1e-6
+    assert rel(u, ur) <= TOL["fp64"], rel(u, ur)
+    assert rel(v, vr) <= TOL["fp64"], rel(v, vr)
+    assert rel(P, Pr) <= 1e-10, rel(P, Pr)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16s"])
+@pytest.mark.parametrize("name", ["tension_32_nh", "corners_nn_45x33", "mixed_37x29", "cantilever_256x32",
+                                  "shape_3x3_mixed"])
+def test_reduced_precision_linear_extrapolation_matches_oracle(L, oracle_mod, name, precision):
+    case, steps, random_init = lin_cases()[name]
+    u0, v0 = initial(case, random_init)
+    u, v, P = run_gpu(L, case.replace(precision=precision), steps, u0, v0)
+    ur, vr, Pr = run_oracle(oracle_mod, case, steps, u0, v0)
+    record(f"{precision}/linear_{name}", u=rel(u, ur), v=rel(v, vr), P=rel(P, Pr))
+    assert rel(u, ur) <= TOL[precision], rel(u, ur)
+
+
+def test_the_reading_reaches_the_kernels(L):
+    """The two readings give different histories (by about 10 % on the 32 x 32
+    tension case at 200 iterations), so the linear result is not the default's."""
+    case, steps, _ = lin_cases()["tension_32_nh"]
+    u_lin = run_gpu(L, case.replace(precision="fp64"), steps)[0]
+    u_own = run_gpu(L, case.replace(precision="fp64", extrap="own"), steps)[0]
+    assert rel(u_lin, u_own) > 1e-2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
+def test_tile_variants_agree_bitwise_with_linear_extrapolation(L, precision):
+    """Every tile variant has its own frame kernel for this reading: all give
+    the same bits."""
+    case, steps, random_init = lin_cases()["corners_nn_45x33"]
+    case = case.replace(precision=precision, nx=101, ny=77)
+    u0, v0 = initial(case, random_init)
+    ref = run_gpu(L, case, steps, u0, v0, variant=0)
+    for v in range(1, len(L.tile_variants(precision))):
+        got = run_gpu(L, case, steps, u0, v0, variant=v)
+        assert all(np.array_equal(a, b) for a, b in zip(got, ref)), v
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6), ("fp16s", 1e-2)])
+@pytest.mark.parametrize("model", ["svk", "nh"])
+def test_homogeneous_stress_is_static_with_linear_extrapolation(L, oracle_mod, model, precision, tol):
+    """Under uniform F every extrapolated value equals the node's own, so the
+    block loaded by P(F) N stays at u = (F - I) X with this reading too."""
+    from test_oracle_pins import homogeneous_case
+    case, u0, P = homogeneous_case(I, oracle_mod, model, "linear")
+    u, v, Pf = run_gpu(L, case.replace(precision=precision), 200, u0, None)
+    scale = np.abs(u0).max()
+    assert np.abs(u - u0).max() <= tol * scale
+    assert np.abs(Pf - P.reshape(4)).max() <= tol * 5 * np.abs(P).max()
+
+
+def test_bending_wave_blows_up_at_the_oracles_iteration(L, oracle_mod):
+    """The paper's 160 x 40 bending wave goes non-finite under this reading
+    (iteration 227 in the oracle); the GPU finds the same iteration (its
+    monitor runs after every iteration; the oracle's fields are checked after
+    every iteration near the end)."""
+    case = I.paper_wave(0.55).replace(extrap="linear", precision="fp64")
+    steps = int(round(12.0 / oracle_mod.params(case)["dt"]))
+    o = oracle_mod.OracleSim(case)
+    k_ora = None
+    for k in range(1, steps + 1):
+        o.step(1)
+        if k >= 150 and not all(np.isfinite(a).all() for a in o.fields()):
+            k_ora = k
+            break
+    assert k_ora is not None
+    sim = L.Simulation(case, monitor_interval=1, graph_chunk=0)
+    try:
+        sim.step(steps)
+        sim.sync()
+    except L.LbsError:
+        pass
+    k_gpu = sim.unstable_iteration
+    sim.close()
+    assert abs(k_gpu - k_ora) <= 1, (k_gpu, k_ora)
+
+
+def test_server_mixes_both_readings(L):
+    """Lattices with and without the linear reading share one batch (its frame
+    tiles then run the linear kernel, which checks each lattice's setting):
+    each result equals the same lattice run alone, bitwise."""
+    trac = I.Edge("neumann", "linear_ramp", (0.01, -0.004), 0, 60)
+    base = [I.tension(32, 32, 150, ramp=100, model="nh"),
+            I.Case("m", 70, 45, 120, model="svk", nu=0.2, edges=(I.CLAMPED, trac, I.FREE, I.FREE)),
+            I.Case("c", 45, 33, 90, model="nh", nu=0.2, edges=(trac, I.FREE, trac, I.FREE))]
+    cases = [c.replace(extrap=e) for c in base for e in ("own", "linear")]
+    with L.Server(precision="fp32", chunk=32) as srv:
+        tickets = [srv.submit(c) for c in cases]
+        srv.drain(120)
+        results = [srv.result(t) for t in tickets]
+    for c, (u, v, P, rc) in zip(cases, results):
+        assert rc == L.OK
+        with L.Simulation(c) as s:
+            s.step(c.nsteps)
+            s.sync()
+            ua, va, Pa = s.fields()
+        assert np.array_equal(u, ua) and np.array_equal(v, va) and np.array_equal(P, Pa), (c.name, c.extrap)

@@ -432,20 +432,52 @@ def test_listing_order_is_unstable_where_text_order_is_not(oracle_mod):
     assert not amp["listing"] < 1.0
 
 
-def test_mirror_symmetry(oracle_mod):
+@pytest.mark.parametrize("extrap", ["own", "linear"])
+def test_mirror_symmetry(oracle_mod, extrap):
     """Tension with a clamped left edge and a normal traction on the right is
-    symmetric about the horizontal mid-line: u_x even, u_y odd."""
-    case = I.tension(10, 9, 0, ramp=50, model="nh")
+    symmetric about the horizontal mid-line: u_x even, u_y odd (with either
+    reading of the wall extrapolation: a bottom wall taking its inner node
+    from the wrong side breaks it)."""
+    case = I.tension(10, 9, 0, ramp=50, model="nh").replace(extrap=extrap)
     s, (u, v, P) = run(oracle_mod, case, None, None, 120)
     assert np.abs(u).max() > 1e-3
     np.testing.assert_allclose(u[:, :, 0], u[::-1, :, 0], atol=1e-14)
     np.testing.assert_allclose(u[:, :, 1], -u[::-1, :, 1], atol=1e-14)
 
 
-def test_transpose_symmetry(oracle_mod):
+@pytest.mark.parametrize("extrap", ["own", "linear"])
+def test_mirror_symmetry_left_right(oracle_mod, extrap):
+    """Opposite normal tractions on the left and right edges, both free
+    elsewhere: the solution is mirror symmetric about the vertical mid-line,
+    u_x odd and u_y even, so the left and right walls (and their inner nodes
+    under the linear reading) are treated alike."""
+    left = I.Edge("neumann", "linear_ramp", (-0.02, 0.0), 0, 40)
+    right = I.Edge("neumann", "linear_ramp", (0.02, 0.0), 0, 40)
+    case = I.Case("lr", 11, 8, 0, model="nh", nu=0.2, edges=(left, right, I.FREE, I.FREE), extrap=extrap)
+    s, (u, v, P) = run(oracle_mod, case, None, None, 90)
+    assert np.abs(u).max() > 1e-3
+    np.testing.assert_allclose(u[:, :, 0], -u[:, ::-1, 0], atol=1e-14)
+    np.testing.assert_allclose(u[:, :, 1], u[:, ::-1, 1], atol=1e-14)
+
+
+def test_linear_reading_uses_its_own_inner_nodes(oracle_mod):
+    """The two readings agree while the fields next to the walls are uniform
+    and part once they vary: on a tension case the linear reading changes u
+    (its wall values are not the node's own), and by a small amount against
+    the size of u (the correction is half a node's difference)."""
+    case = I.tension(16, 12, 0, ramp=50, model="nh")
+    _, (u0, _, _) = run(oracle_mod, case, None, None, 100)
+    _, (u1, _, _) = run(oracle_mod, case.replace(extrap="linear"), None, None, 100)
+    d = np.abs(u1 - u0).max() / np.abs(u0).max()
+    assert 1e-4 < d < 0.2, d
+
+
+@pytest.mark.parametrize("extrap", ["own", "linear"])
+def test_transpose_symmetry(oracle_mod, extrap):
     """Swapping the roles of x and y (edges, components, lattice) gives the
-    transposed solution: no axis is treated differently from the other."""
-    a = I.tension(9, 7, 0, ramp=40, model="svk")
+    transposed solution: no axis is treated differently from the other (with
+    either reading of the wall extrapolation)."""
+    a = I.tension(9, 7, 0, ramp=40, model="svk").replace(extrap=extrap)
     e = a.edges
     right = e[1]
     top = I.Edge(right.kind, right.shape, (right.amp[1], right.amp[0]), right.t0, right.t1)
@@ -455,11 +487,13 @@ def test_transpose_symmetry(oracle_mod):
     np.testing.assert_allclose(ub.transpose(1, 0, 2)[:, :, ::-1], ua, atol=1e-14)
 
 
-def test_linear_material_scales_linearly(oracle_mod):
+@pytest.mark.parametrize("extrap", ["own", "linear"])
+def test_linear_material_scales_linearly(oracle_mod, extrap):
     """With the linear material every step is linear in (state, loads):
-    doubling the traction doubles the displacement."""
-    base = I.tension(8, 8, 0, ramp=30, model="le", nu=0.2, peak=1e-3)
-    dbl = I.tension(8, 8, 0, ramp=30, model="le", nu=0.2, peak=2e-3)
+    doubling the traction doubles the displacement (both wall readings are
+    linear in the node values)."""
+    base = I.tension(8, 8, 0, ramp=30, model="le", nu=0.2, peak=1e-3).replace(extrap=extrap)
+    dbl = I.tension(8, 8, 0, ramp=30, model="le", nu=0.2, peak=2e-3).replace(extrap=extrap)
     _, (u1, _, _) = run(oracle_mod, base, None, None, 60)
     _, (u2, _, _) = run(oracle_mod, dbl, None, None, 60)
     assert np.abs(u1).max() > 1e-6
