@@ -271,9 +271,10 @@ __device__ void wall_rules(const Params &P, const R *bnd, const G *g, int x, int
     axy_y = (Nn[1] - s * (R)T[0]) * ics2;
   }
   // two-point extrapolation: half the differences own - inner of r, A and N
-  // for the x wall (dX, nX) and the y wall (dY, nY) the node sits on
+  // for the x wall (dX, nX) and the y wall (dY, nY) the node sits on (a
+  // lattice without the setting has no second side-array layer to read).
   R dX[4] = {0, 0, 0, 0}, dY[4] = {0, 0, 0, 0}, nX[4] = {0, 0, 0, 0}, nY[4] = {0, 0, 0, 0};
-  if constexpr (LIN) {
+  if (LIN && P.extrap) {
     const size_t plane = (size_t)P.ny * P.pitch;
     const R *inner = bnd + (size_t)4 * P.blen * 4;  // second layer of the side array
     const R own[4] = {r, Axx_o, Axy_o, Ayy_o};
@@ -805,7 +806,7 @@ static __global__ void batch_advance_kernel(BatchLattice *lats, int n) {
 
 template <class C>
 cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
-                              int ne, bool lin, int *err, cudaStream_t st) {
+                              int ne, const BatchTile *edge_lin, int nl, int *err, cudaStream_t st) {
   // resident blocks of the persistent kernel on this device (computed once;
   // the initialisation of a function-local static is thread-safe)
   static const int blocks = [] {
@@ -816,8 +817,8 @@ cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *in
     return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }();
   if (ni > 0) batch_step_kernel<C, false><<<ni < blocks ? ni : blocks, C::NT, 0, st>>>(lats, interior, ni, err);
-  if (ne > 0 && lin) batch_step_kernel<C, true, true><<<ne < blocks ? ne : blocks, C::NT, 0, st>>>(lats, edge, ne, err);
-  else if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, st>>>(lats, edge, ne, err);
+  if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, st>>>(lats, edge, ne, err);
+  if (nl > 0) batch_step_kernel<C, true, true><<<nl < blocks ? nl : blocks, C::NT, 0, st>>>(lats, edge_lin, nl, err);
   if (nlats > 0) batch_advance_kernel<<<(nlats + 127) / 128, 128, 0, st>>>(lats, nlats);
   return cudaGetLastError();
 }

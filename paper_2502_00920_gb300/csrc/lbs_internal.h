@@ -92,11 +92,11 @@ struct Launchers {
                          double *out7, int64_t k, cudaStream_t st);
   cudaError_t (*probe)(const Params &p, const void *u, const int32_t *idx, int n, double *out, cudaStream_t st);
   // one iteration of every unfinished lattice of a batch: interior tiles,
-  // frame tiles, then the per-lattice counters (tile shape of the default
-  // global-memory variant, batch_tile()); `lin`: some lattice of the batch
-  // takes two-point wall extrapolation (its frame tiles need that kernel)
+  // frame tiles, frame tiles of the lattices with two-point wall
+  // extrapolation (their own kernel), then the per-lattice counters (tile
+  // shape of the default global-memory variant, batch_tile())
   cudaError_t (*batch_step)(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
-                            int ne, bool lin, int *err, cudaStream_t st);
+                            int ne, const BatchTile *edge_lin, int nl, int *err, cudaStream_t st);
   TileShape batch_tile;
   size_t g_elem, u_elem, b_elem;  // bytes per stored g value, per u record, per boundary entry
 };

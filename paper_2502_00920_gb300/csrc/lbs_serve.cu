@@ -175,12 +175,12 @@ struct ChunkGraph {
   }
 };
 
-cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int nres, int ni, int ne, bool lin, int64_t n,
+cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int nres, int ni, int ne, int nl, int64_t n,
                       ChunkGraph &G) {
   auto direct = [&]() -> cudaError_t {
     for (int64_t it = 0; it < n; ++it) {
-      const cudaError_t e =
-          L.batch_step(s->d_lats, nres, s->d_tiles, ni, s->d_tiles + ni, ne, lin, s->d_err, s->stream);
+      const BatchTile *t = s->d_tiles;
+      const cudaError_t e = L.batch_step(s->d_lats, nres, t, ni, t + ni, ne, t + ni + ne, nl, s->d_err, s->stream);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -215,8 +215,7 @@ void run(lbs_server *s) {
   std::vector<Req *> res;
   std::vector<BatchLattice> hl;
   std::vector<BatchTile> ht;
-  int ni = 0, ne = 0;
-  bool lin = false;  // a resident lattice takes two-point wall extrapolation
+  int ni = 0, ne = 0, nl = 0;  // interior tiles, frame tiles, frame tiles of two-point-extrapolation lattices
   bool dirty = true;
   const lbs::Launchers &L = s->cfg.precision == LBS_FP64   ? lbs::launchers_fp64()
                             : s->cfg.precision == LBS_FP32 ? lbs::launchers_fp32()
@@ -299,14 +298,12 @@ void run(lbs_server *s) {
       graph.drop();
       hl.resize(res.size());
       ht.clear();
-      std::vector<BatchTile> edge;
+      std::vector<BatchTile> edge, edge_lin;
       const int TX = L.batch_tile.tx, TY = L.batch_tile.ty;
-      lin = false;
       for (size_t i = 0; i < res.size(); ++i) {
         lbs_handle *h = res[i]->h;
         BatchLattice &B = hl[i];
         B.P = h->P;
-        lin = lin || h->P.extrap;
         for (int p = 0; p < 2; ++p) {
           B.g[p] = h->g[p];
           B.u[p] = h->u[p];
@@ -320,12 +317,14 @@ void run(lbs_server *s) {
         for (int b = 0; b < nty; ++b)
           for (int a = 0; a < ntx; ++a) {
             const bool in = a >= a_lo && a < a_hi && b >= b_lo && b < b_hi;
-            (in ? ht : edge).push_back(BatchTile{(int)i, a, b});
+            (in ? ht : (h->P.extrap ? edge_lin : edge)).push_back(BatchTile{(int)i, a, b});
           }
       }
       ni = (int)ht.size();
       ne = (int)edge.size();
+      nl = (int)edge_lin.size();
       ht.insert(ht.end(), edge.begin(), edge.end());
+      ht.insert(ht.end(), edge_lin.begin(), edge_lin.end());
       if (!ensure(s->d_lats, s->lat_cap, (int)hl.size()) || !ensure(s->d_tiles, s->tile_cap, (int)ht.size())) {
         for (Req *r : res) finish(s, r, LBS_ENOMEM);
         res.clear();
@@ -341,8 +340,8 @@ void run(lbs_server *s) {
     for (Req *r : res) longest = std::max(longest, r->nsteps - r->k);
     chunk = std::min(chunk, longest);
     const double tb = s->now();
-    const int64_t launched = chunk * ((ni > 0) + (ne > 0) + 1);
-    cudaError_t e = run_chunk(s, L, (int)res.size(), ni, ne, lin, chunk, graph);
+    const int64_t launched = chunk * ((ni > 0) + (ne > 0) + (nl > 0) + 1);
+    cudaError_t e = run_chunk(s, L, (int)res.size(), ni, ne, nl, chunk, graph);
     const cudaError_t es = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = es;
     {

@@ -30,12 +30,15 @@ def L():
 
 
 def lin_cases():
-    """(case, iterations, initial state) with the linear reading.  The 32 x 32
-    tension case runs 200 iterations: under this reading it goes non-finite
-    at iteration 372 (oracle)."""
+    """(case, iterations, initial state) with the linear reading, each history
+    ending well before the reading's own instability sets in: the 32 x 32
+    tension case goes non-finite at iteration 372 and the 64 x 40 case with a
+    periodic x axis near 225 (oracle), where rounding differences of 1e-16
+    have already grown a thousandfold by iteration 200; they run 200 and 150
+    iterations."""
     out = {}
     for name, steps in (("tension_32_nh", 200), ("corners_nn_45x33", 150), ("mixed_37x29", 200),
-                        ("periodic_x_walls_y_64x40", 200), ("cantilever_256x32", 300), ("walls_150x100_nh", 200)):
+                        ("periodic_x_walls_y_64x40", 150), ("cantilever_256x32", 300), ("walls_150x100_nh", 200)):
         case, _, random_init = CASES()[name]
         out[name] = (case.replace(extrap="linear"), steps, random_init)
     for name in ("3x3_mixed", "3x40_walls", "40x3_walls", "17x9_sub_tile", "65x49_one_more", "rho2.5_E3"):
@@ -135,14 +138,14 @@ def test_bending_wave_blows_up_at_the_oracles_iteration(L, oracle_mod):
 
 
 def test_server_mixes_both_readings(L):
-    """Lattices with and without the linear reading share one batch (its frame
-    tiles then run the linear kernel, which checks each lattice's setting):
-    each result equals the same lattice run alone, bitwise."""
+    """Lattices with and without the linear reading share one batch (the frame
+    tiles of each kind run in their own kernel): each result equals the same
+    lattice run alone, bitwise."""
     trac = I.Edge("neumann", "linear_ramp", (0.01, -0.004), 0, 60)
     base = [I.tension(32, 32, 150, ramp=100, model="nh"),
             I.Case("m", 70, 45, 120, model="svk", nu=0.2, edges=(I.CLAMPED, trac, I.FREE, I.FREE)),
             I.Case("c", 45, 33, 90, model="nh", nu=0.2, edges=(trac, I.FREE, trac, I.FREE))]
-    cases = [c.replace(extrap=e) for c in base for e in ("own", "linear")]
+    cases = [c.replace(extrap=e, precision="fp32") for c in base for e in ("own", "linear")]
     with L.Server(precision="fp32", chunk=32) as srv:
         tickets = [srv.submit(c) for c in cases]
         srv.drain(120)
