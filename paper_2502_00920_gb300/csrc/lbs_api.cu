@@ -204,6 +204,28 @@ static Sizes sizes_of(const Params &p, const Launchers &L) {
   return s;
 }
 
+// Device room for host transfers without allocating: the g and u buffers of
+// the parity the state is not in.  The next iteration overwrites them without
+// reading them, so set_initial stages u0, v0 there and fields stages its
+// outputs there.  Blocks are handed out 256-byte aligned.
+struct Scratch {
+  char *base[2];
+  size_t cap[2], used[2];
+};
+static Scratch scratch_of(const lbs_handle *h, int parity) {
+  const Sizes sz = sizes_of(h->P, *h->L);
+  return Scratch{{(char *)h->g[parity], (char *)h->u[parity]}, {sz.g, sz.u}, {0, 0}};
+}
+static double *scratch_take(Scratch &s, size_t bytes) {
+  for (int i = 0; i < 2; ++i)
+    if (s.used[i] <= s.cap[i] && s.cap[i] - s.used[i] >= bytes) {
+      char *p = s.base[i] + s.used[i];
+      s.used[i] += (bytes + 255) / 256 * 256;
+      return (double *)p;
+    }
+  return nullptr;
+}
+
 __global__ void set_counter_kernel(int64_t *k, int64_t v) { *k = v; }
 __global__ void add_counter_kernel(int64_t *k, int64_t d) { *k += d; }
 
@@ -524,16 +546,28 @@ int lbs_set_initial_device(lbs_handle *h, const double *u0, const double *v0) {
 int lbs_set_initial(lbs_handle *h, const double *u0, const double *v0) {
   if (!h) return fail(LBS_EINVAL, "null handle");
   const size_t bytes = (size_t)h->P.nx * h->P.ny * 2 * sizeof(double);
-  double *du = nullptr, *dv = nullptr;
+  // the initialisation writes the buffers of parity 0: stage u0, v0 in those
+  // of parity 1 (allocate only what does not fit there)
+  Scratch sc = scratch_of(h, 1);
+  const double *hosts[2] = {u0, v0};
+  double *dev[2] = {nullptr, nullptr};
+  bool owned[2] = {false, false};
   int rc = LBS_OK;
-  if (u0 && !(du = (double *)dev_alloc(h->alloc, bytes, h->stream))) rc = fail(LBS_ENOMEM, "initial field buffer");
-  if (!rc && v0 && !(dv = (double *)dev_alloc(h->alloc, bytes, h->stream))) rc = fail(LBS_ENOMEM, "initial field buffer");
-  if (!rc && du && cudaMemcpyAsync(du, u0, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) rc = LBS_ECUDA;
-  if (!rc && dv && cudaMemcpyAsync(dv, v0, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) rc = LBS_ECUDA;
-  if (!rc) rc = lbs_set_initial_device(h, du, dv);
+  for (int i = 0; i < 2 && !rc; ++i) {
+    if (!hosts[i]) continue;
+    dev[i] = scratch_take(sc, bytes);
+    if (!dev[i]) {
+      dev[i] = (double *)dev_alloc(h->alloc, bytes, h->stream);
+      owned[i] = dev[i] != nullptr;
+      if (!dev[i]) rc = fail(LBS_ENOMEM, "initial field buffer");
+    }
+    if (!rc && cudaMemcpyAsync(dev[i], hosts[i], bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      rc = fail(LBS_ECUDA, "initial field copy");
+  }
+  if (!rc) rc = lbs_set_initial_device(h, dev[0], dev[1]);
   if (cudaStreamSynchronize(h->stream) != cudaSuccess && !rc) rc = fail(LBS_ECUDA, "initialisation failed");
-  dev_free(h->alloc, du, h->stream);
-  dev_free(h->alloc, dv, h->stream);
+  for (int i = 0; i < 2; ++i)
+    if (owned[i]) dev_free(h->alloc, dev[i], h->stream);
   return rc;
 }
 
@@ -598,21 +632,37 @@ int lbs_fields_device(lbs_handle *h, double *u, double *v, double *P) {
 int lbs_fields(lbs_handle *h, double *u, double *v, double *P) {
   if (!h) return fail(LBS_EINVAL, "null handle");
   const size_t n = (size_t)h->P.nx * h->P.ny;
-  double *bufs[3] = {nullptr, nullptr, nullptr};
   double *hosts[3] = {u, v, P};
-  const size_t widths[3] = {2, 2, 4};
+  const size_t bytes[3] = {n * 2 * sizeof(double), n * 2 * sizeof(double), n * 4 * sizeof(double)};
+  bool done[3] = {!u, !v, !P};
+  double *owned[3] = {nullptr, nullptr, nullptr};
   int rc = LBS_OK;
-  for (int i = 0; i < 3 && !rc; ++i)
-    if (hosts[i] && !(bufs[i] = (double *)dev_alloc(h->alloc, n * widths[i] * sizeof(double), h->stream)))
-      rc = fail(LBS_ENOMEM, "field buffer");
-  if (!rc) rc = lbs_fields_device(h, bufs[0], bufs[1], bufs[2]);
-  for (int i = 0; i < 3 && !rc; ++i)
-    if (hosts[i] &&
-        cudaMemcpyAsync(hosts[i], bufs[i], n * widths[i] * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
-            cudaSuccess)
-      rc = fail(LBS_ECUDA, "field copy");
+  // passes over the fields: each stages what fits in the buffers of the
+  // other parity (allocating one field that fits nowhere), then copies it
+  // out; stream order keeps a pass from overwriting the last one's copies
+  while (!rc && !(done[0] && done[1] && done[2])) {
+    Scratch sc = scratch_of(h, h->parity ^ 1);
+    double *dev[3] = {nullptr, nullptr, nullptr};
+    bool any = false;
+    for (int i = 0; i < 3; ++i)
+      if (!done[i] && (dev[i] = scratch_take(sc, bytes[i]))) any = true;
+    if (!any) {
+      const int i = !done[0] ? 0 : (!done[1] ? 1 : 2);
+      if (!(owned[i] = dev[i] = (double *)dev_alloc(h->alloc, bytes[i], h->stream))) {
+        rc = fail(LBS_ENOMEM, "field buffer");
+        break;
+      }
+    }
+    rc = lbs_fields_device(h, dev[0], dev[1], dev[2]);
+    for (int i = 0; i < 3 && !rc; ++i) {
+      if (!dev[i]) continue;
+      if (cudaMemcpyAsync(hosts[i], dev[i], bytes[i], cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        rc = fail(LBS_ECUDA, "field copy");
+      done[i] = true;
+    }
+  }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess && !rc) rc = fail(LBS_ECUDA, "field output failed");
-  for (int i = 0; i < 3; ++i) dev_free(h->alloc, bufs[i], h->stream);
+  for (int i = 0; i < 3; ++i) dev_free(h->alloc, owned[i], h->stream);
   return rc;
 }
 
