@@ -806,7 +806,8 @@ static __global__ void batch_advance_kernel(BatchLattice *lats, int n) {
 
 template <class C>
 cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
-                              int ne, const BatchTile *edge_lin, int nl, int *err, cudaStream_t st) {
+                              int ne, const BatchTile *edge_lin, int nl, int *err, cudaStream_t st,
+                              const BatchFork *fork) {
   // resident blocks of the persistent kernel on this device (computed once;
   // the initialisation of a function-local static is thread-safe)
   static const int blocks = [] {
@@ -816,9 +817,23 @@ cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *in
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<C, false>, C::NT, 0);
     return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }();
+  // the frame tiles (few, long, latency-bound) run beside the interior tiles
+  // when a side stream is given: both read iteration k and write k + 1 of
+  // disjoint nodes; the counters advance once both have finished
+  const bool split = fork && ni > 0 && (ne > 0 || nl > 0);
+  cudaStream_t fs = st;
+  if (split) {
+    cudaEventRecord(fork->fork, st);
+    cudaStreamWaitEvent(fork->side, fork->fork, 0);
+    fs = fork->side;
+  }
+  if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, err);
+  if (nl > 0) batch_step_kernel<C, true, true><<<nl < blocks ? nl : blocks, C::NT, 0, fs>>>(lats, edge_lin, nl, err);
   if (ni > 0) batch_step_kernel<C, false><<<ni < blocks ? ni : blocks, C::NT, 0, st>>>(lats, interior, ni, err);
-  if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, st>>>(lats, edge, ne, err);
-  if (nl > 0) batch_step_kernel<C, true, true><<<nl < blocks ? nl : blocks, C::NT, 0, st>>>(lats, edge_lin, nl, err);
+  if (split) {
+    cudaEventRecord(fork->join, fs);
+    cudaStreamWaitEvent(st, fork->join, 0);
+  }
   if (nlats > 0) batch_advance_kernel<<<(nlats + 127) / 128, 128, 0, st>>>(lats, nlats);
   return cudaGetLastError();
 }

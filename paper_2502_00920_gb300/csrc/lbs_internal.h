@@ -71,6 +71,13 @@ struct BatchTile {
   int lat, a, b;
 };
 
+// A second stream and two events with which one batch iteration runs its
+// frame-tile launches beside the interior-tile launch (fork, join).
+struct BatchFork {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+};
+
 // Launchers, one set per precision (kernels_fp*.cu).  `variant` picks a tile
 // shape (0 = default).  Return a cudaError_t of the launch.
 struct Launchers {
@@ -95,8 +102,11 @@ struct Launchers {
   // frame tiles, frame tiles of the lattices with two-point wall
   // extrapolation (their own kernel), then the per-lattice counters (tile
   // shape of the default global-memory variant, batch_tile())
+  // (`fork`, if given, runs the frame tiles on its side stream, concurrently
+  // with the interior tiles; the counters advance after both)
   cudaError_t (*batch_step)(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
-                            int ne, const BatchTile *edge_lin, int nl, int *err, cudaStream_t st);
+                            int ne, const BatchTile *edge_lin, int nl, int *err, cudaStream_t st,
+                            const BatchFork *fork);
   TileShape batch_tile;
   size_t g_elem, u_elem, b_elem;  // bytes per stored g value, per u record, per boundary entry
 };

@@ -60,6 +60,7 @@ struct lbs_server {
   lbs_server_stats st;
   // owned by the worker thread
   cudaStream_t stream = nullptr;
+  lbs::BatchFork fork = {nullptr, nullptr, nullptr};  // frame tiles beside interior tiles
   BatchLattice *d_lats = nullptr;
   int lat_cap = 0;
   BatchTile *d_tiles = nullptr;
@@ -180,7 +181,8 @@ cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int nres, int ni, 
   auto direct = [&]() -> cudaError_t {
     for (int64_t it = 0; it < n; ++it) {
       const BatchTile *t = s->d_tiles;
-      const cudaError_t e = L.batch_step(s->d_lats, nres, t, ni, t + ni, ne, t + ni + ne, nl, s->d_err, s->stream);
+      const cudaError_t e =
+          L.batch_step(s->d_lats, nres, t, ni, t + ni, ne, t + ni + ne, nl, s->d_err, s->stream, &s->fork);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -390,9 +392,15 @@ int lbs_server_create(const lbs_server_config *cfg, lbs_server **out) {
   s->t0 = Clock::now();
   if (cudaGetDevice(&s->device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->fork.side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->fork.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->fork.join, cudaEventDisableTiming) != cudaSuccess ||
       cudaMalloc(&s->d_err, sizeof(int)) != cudaSuccess || cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->fork.side) cudaStreamDestroy(s->fork.side);
+    if (s->fork.fork) cudaEventDestroy(s->fork.fork);
+    if (s->fork.join) cudaEventDestroy(s->fork.join);
     delete s;
     lbs::set_error("server: CUDA set-up failed");
     return LBS_ECUDA;
@@ -538,6 +546,9 @@ int lbs_server_destroy(lbs_server *s) {
   if (s->d_tiles) cudaFree(s->d_tiles);
   if (s->d_err) cudaFree(s->d_err);
   if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->fork.side) cudaStreamDestroy(s->fork.side);
+  if (s->fork.fork) cudaEventDestroy(s->fork.fork);
+  if (s->fork.join) cudaEventDestroy(s->fork.join);
   delete s;
   return LBS_OK;
 }

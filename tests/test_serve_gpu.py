@@ -94,17 +94,20 @@ def test_admission_respects_budget(L):
 
 def test_continuous_admission(L):
     """Requests arriving while others are on the GPU join the running batch."""
-    # stable over its whole history in the oracle (the same load at nu = 0.3
-    # and peak 0.2 goes non-finite between 1000 and 2000 iterations)
-    long = I.tension(512, 256, 3000, ramp=500, model="nh", nu=0.2, peak=0.05)
+    # stable over its whole history in the oracle (finite to beyond 7000
+    # iterations; the same load at nu = 0.3 and peak 0.2 goes non-finite
+    # between 1000 and 2000 iterations)
+    long = I.tension(512, 256, 6500, ramp=500, model="nh", nu=0.2, peak=0.05)
     short = [I.tension(64, 48, 200, ramp=50, model="svk", nu=0.1) for _ in range(4)]
     with L.Server(precision="fp32", chunk=32) as srv:
         t_long = srv.submit(long)
-        time.sleep(0.05)
+        t_wait = time.time()
+        while srv.poll(t_long)["iterations"] == 0 and time.time() - t_wait < 30:
+            time.sleep(0.001)  # the long one is on the GPU
         ts = []
         for c in short:
             ts.append(srv.submit(c))
-            time.sleep(0.01)
+            time.sleep(0.002)
         srv.drain(120)
         il = srv.poll(t_long)
         infos = [srv.poll(t) for t in ts]
