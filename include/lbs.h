@@ -145,7 +145,9 @@ int lbs_set_stream(lbs_handle *h, void *cuda_stream);
  * either may be NULL for zero).  Resets the iteration counter to 0 and builds
  * the initial distributions of Alg. 1 "Initialise": r0 = -rho0 tr H0,
  * Pi0 = Pi(H0) = -mu (H0 + H0^T + tr H0 I), f0 = feq(r0, rho0 v0 - dt/2 S0, Pi0).
- * Synchronous. */
+ * The host arrays are copied into the handle's second state buffers (which
+ * the first iteration overwrites) where they fit, else into a temporary
+ * device buffer.  Synchronous. */
 int lbs_set_initial(lbs_handle *h, const double *u0, const double *v0);
 
 /* As lbs_set_initial with device pointers; asynchronous on the stream. */
@@ -165,7 +167,11 @@ int lbs_sync(lbs_handle *h);
 
 /* Fields at the current iteration into caller-owned HOST buffers (any may be
  * NULL): u, the velocity v = j / rho0 with j = sum_q c_q f_q + dt/2 S (the
- * momentum of Alg. 1 at the current time) and P(H(u)).  Synchronous. */
+ * momentum of Alg. 1 at the current time) and P(H(u)).  The fields are staged
+ * in the state buffers the next iteration overwrites (in more than one pass
+ * when they do not fit at once; a field that fits nowhere, P under
+ * LBS_FP16S, gets a temporary device buffer); the state itself is untouched.
+ * Synchronous. */
 int lbs_fields(lbs_handle *h, double *u, double *v, double *P);
 
 /* As lbs_fields into caller-owned DEVICE buffers; asynchronous. */
