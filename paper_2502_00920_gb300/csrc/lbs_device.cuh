@@ -232,8 +232,8 @@ __device__ inline void edge_value(const Params &P, int e, int64_t k, double out[
 // wall, v_in the value at the next node inwards along that wall's normal: r
 // and Pi from that node's own g, N from the side array's second layer.
 template <class R, class G, bool LIN>
-__device__ void wall_rules(const Params &P, const R *bnd, const G *g, int x, int y, int64_t k, const R g0[9],
-                           unsigned mask, R f[9], R gsc) {
+__device__ void wall_rules(const Params &P, const R *bnd, const G *g, const double (*sev)[2], int x, int y,
+                           const R g0[9], unsigned mask, R f[9], R gsc) {
   int xw = -1, yw = -1;
   if (!P.per_x) xw = (x == 0) ? kLeft : ((x == P.nx - 1) ? kRight : -1);
   if (!P.per_y) yw = (y == 0) ? kBottom : ((y == P.ny - 1) ? kTop : -1);
@@ -256,16 +256,14 @@ __device__ void wall_rules(const Params &P, const R *bnd, const G *g, int x, int
   R Axx_x = 0, axy_x = 0, Ayy_y = 0, axy_y = 0;
   if (xn) {
     const R *Nn = bnd + ((size_t)xw * P.blen + y) * 4;  // N11, N12, N21, N22
-    double T[2];
-    edge_value(P, xw, k, T);
+    const double *T = sev[xw];
     const R s = (xw == kRight) ? R(1) : R(-1);
     Axx_x = (Nn[0] - s * (R)T[0]) * ics2;
     axy_x = (Nn[2] - s * (R)T[1]) * ics2;
   }
   if (yn) {
     const R *Nn = bnd + ((size_t)yw * P.blen + x) * 4;
-    double T[2];
-    edge_value(P, yw, k, T);
+    const double *T = sev[yw];
     const R s = (yw == kTop) ? R(1) : R(-1);
     Ayy_y = (Nn[3] - s * (R)T[1]) * ics2;
     axy_y = (Nn[1] - s * (R)T[0]) * ics2;
@@ -319,13 +317,12 @@ __device__ void wall_rules(const Params &P, const R *bnd, const G *g, int x, int
     if (dxw || dyw) {
       double js[2];
       if (dxw && dyw) {
-        double a[2], b[2];
-        edge_value(P, xw, k, a);
-        edge_value(P, yw, k, b);
+        const double *a = sev[xw], *b = sev[yw];
         js[0] = 0.5 * (a[0] + b[0]);
         js[1] = 0.5 * (a[1] + b[1]);
       } else {
-        edge_value(P, dxw ? xw : yw, k, js);
+        js[0] = sev[dxw ? xw : yw][0];
+        js[1] = sev[dxw ? xw : yw][1];
       }
       f[q] = g0[qb] + R(2) * wq<R>(q) * cj * (R(ex(q)) * (R)js[0] + R(ey(q)) * (R)js[1]);
     } else if constexpr (!LIN) {
@@ -454,8 +451,9 @@ __device__ __forceinline__ bool locate(const Params &P, int &x, int &y) {
 // LIN: the two-point wall extrapolation (lattices with P.extrap set).
 template <class Pr, bool EDGE, bool LIN>
 __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *__restrict__ g, const typename Pr::real *bnd,
-                                       int x, int y, int64_t k, typename Pr::real inv, typename Pr::real f[9],
-                                       typename Pr::real &gx, typename Pr::real &gy, typename Pr::real gsc) {
+                                       const double (*sev)[2], int x, int y, typename Pr::real inv,
+                                       typename Pr::real f[9], typename Pr::real &gx, typename Pr::real &gy,
+                                       typename Pr::real gsc) {
   using R = typename Pr::real;
   const size_t plane = (size_t)P.ny * P.pitch;
   const size_t idx = (size_t)y * P.pitch + x;
@@ -488,7 +486,7 @@ __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *_
         f[q] = gload(g, q * plane + (size_t)sy * P.pitch + sx, inv);
       }
     }
-    if (mask) wall_rules<R, typename Pr::gs, LIN>(P, bnd, g, x, y, k, g0, mask, f, gsc);
+    if (mask) wall_rules<R, typename Pr::gs, LIN>(P, bnd, g, sev, x, y, g0, mask, f, gsc);
   }
   gx = (g0[1] - g0[3]) + (g0[5] - g0[6]) + (g0[8] - g0[7]);
   gy = (g0[2] - g0[4]) + (g0[5] - g0[8]) + (g0[6] - g0[7]);
@@ -618,6 +616,13 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
   us *__restrict__ uo = (us *)S.u_out;
   const R *bnd = (const R *)S.b_in;
   const int64_t k = EDGE ? (*S.kptr + S.koff) : 0;
+  // boundary values of the four edges at iteration k, evaluated once per
+  // tile (the wall rules of every wall node read them)
+  __shared__ double sev[4][2];
+  if (EDGE) {
+    if (threadIdx.x < 4) edge_value(P, threadIdx.x, k, sev[threadIdx.x]);
+    __syncthreads();
+  }
   // g is held in units of g * 2^gshift (1 unless FP16 storage)
   const R inv = gscale_inv<typename C::gs, R>(P), scl = gscale<typename C::gs, R>(P);
   const R kap = (R)P.kappa * inv;
@@ -634,7 +639,7 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     int x = x0 + lx, y = y0 + ly;
     if (EDGE && !locate(P, x, y)) continue;
     R gxm, gym;
-    gather<typename C::PrT, EDGE, LIN>(P, g, bnd, x, y, k, inv, f[i], gxm, gym, scl);
+    gather<typename C::PrT, EDGE, LIN>(P, g, bnd, sev, x, y, inv, f[i], gxm, gym, scl);
     const R fx = (f[i][1] - f[i][3]) + (f[i][5] - f[i][6]) + (f[i][8] - f[i][7]);
     const R fy = (f[i][2] - f[i][4]) + (f[i][5] - f[i][8]) + (f[i][6] - f[i][7]);
     sm.u[ly + 2][lx + 2] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
@@ -646,7 +651,7 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     int x = x0 - 2 + rx, y = y0 - 2 + ry;
     if (EDGE && !locate(P, x, y)) continue;
     R ff[9], gxm, gym;
-    gather<typename C::PrT, EDGE, LIN>(P, g, bnd, x, y, k, inv, ff, gxm, gym, scl);
+    gather<typename C::PrT, EDGE, LIN>(P, g, bnd, sev, x, y, inv, ff, gxm, gym, scl);
     const R fx = (ff[1] - ff[3]) + (ff[5] - ff[6]) + (ff[8] - ff[7]);
     const R fy = (ff[2] - ff[4]) + (ff[5] - ff[8]) + (ff[6] - ff[7]);
     sm.u[ry][rx] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
