@@ -31,6 +31,10 @@
  *       "extrapolated to the boundary" is the boundary node's own value; the
  *       (P + Pi(H)) used there is the array as it stands when block 2 runs,
  *       i.e. computed in block 3 of the previous iteration (or at initialisation).
+ *       ORA_EXTRAP_LINEAR selects the other reading: v + (v - v_in)/2 for each
+ *       wall the link crosses, v_in at the next node inwards (the wall lies half
+ *       a spacing beyond the node).  Its pins are the uniform-state, symmetry
+ *       and linearity tests; the factor 1/2 itself is parity unpinned.
  *   R8  corners: each outgoing link takes the rule of the wall it crosses,
  *       with the Pi* of that wall (its other diagonal entry from the node's
  *       own moment); a diagonal link crossing two walls is Dirichlet if either
