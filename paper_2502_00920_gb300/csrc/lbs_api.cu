@@ -250,6 +250,7 @@ StepPtrs ptrs(const lbs_handle *h, int parity, const int64_t *kptr, int64_t koff
   s.tm_g = h->tma ? (const void *)&h->tm_g[parity] : nullptr;
   s.tm_u = h->tma ? (const void *)&h->tm_u[parity] : nullptr;
   s.err = h->errdev;
+  s.fork = h->fork.side ? &h->fork : nullptr;
   return s;
 }
 
@@ -478,6 +479,12 @@ int lbs_create(const lbs_lattice *lat, const lbs_material *mat, const lbs_bcs *b
     cudaGetLastError();
     ok = false;
   }
+  if (ok && (cudaStreamCreateWithFlags(&h->fork.side, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&h->fork.fork, cudaEventDisableTiming) != cudaSuccess ||
+             cudaEventCreateWithFlags(&h->fork.join, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    ok = false;
+  }
   if (!ok) {
     lbs_destroy(h);
     return fail(LBS_ENOMEM, "device allocation of " + std::to_string(2 * (s.g + s.u + s.b)) + " bytes failed");
@@ -514,6 +521,10 @@ int lbs_destroy(lbs_handle *h) {
   dev_free(h->alloc, h->mon_block, h->own_stream);
   if (h->mon_host) cudaFreeHost(h->mon_host);
   if (h->mon_event) cudaEventDestroy(h->mon_event);
+  if (h->fork.side) cudaStreamSynchronize(h->fork.side);
+  if (h->fork.side) cudaStreamDestroy(h->fork.side);
+  if (h->fork.fork) cudaEventDestroy(h->fork.fork);
+  if (h->fork.join) cudaEventDestroy(h->fork.join);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
   return LBS_OK;

@@ -731,6 +731,26 @@ void launch_edge(const Params &P, const StepPtrs &S, int nedge, int ntx, int a_l
   else step_edge_kernel<C, false><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
 }
 
+// longest walk (tiles per persistent block) beside which a frame kernel runs
+constexpr int kForkWalk = 16;
+
+// With a fork (S.fork) the frame kernel of an iteration runs on the fork's
+// side stream beside the interior kernel: both read iteration k and write
+// disjoint nodes of k + 1.  fork_begin() records the fork point on `st` and
+// returns whether the side stream is used; fork_end() makes `st` wait for it.
+inline bool fork_begin(const StepPtrs &S, cudaStream_t st, bool want) {
+  if (!S.fork || !want) return false;
+  cudaEventRecord(S.fork->fork, st);
+  cudaStreamWaitEvent(S.fork->side, S.fork->fork, 0);
+  return true;
+}
+
+inline void fork_end(const StepPtrs &S, cudaStream_t st, bool on) {
+  if (!on) return;
+  cudaEventRecord(S.fork->join, S.fork->side);
+  cudaStreamWaitEvent(st, S.fork->join, 0);
+}
+
 // interior tile range [a_lo, a_hi) x [b_lo, b_hi): R2 of the tile and the
 // streaming sources of R2 (a 3-node frame) stay clear of the walls and of the
 // lattice end.  Empty ranges are normalised to (0, 0).
@@ -758,9 +778,12 @@ cudaError_t launch_step(const Params &P, const StepPtrs &S, cudaStream_t st) {
   int a_lo, a_hi, b_lo, b_hi;
   interior_range(P.nx, P.ny, C::TX, C::TY, a_lo, a_hi, b_lo, b_hi);
   const int ni = a_hi - a_lo, nj = b_hi - b_lo;
-  if (ni > 0 && nj > 0) step_interior_kernel<C><<<dim3(ni, nj), C::NT, 0, st>>>(P, S, a_lo, b_lo);
   const int nedge = ntx * nty - ni * nj;
-  launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
+  const bool beside = fork_begin(S, st, ni > 0 && nj > 0 && nedge > 0);
+  if (beside) launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, S.fork->side);
+  if (ni > 0 && nj > 0) step_interior_kernel<C><<<dim3(ni, nj), C::NT, 0, st>>>(P, S, a_lo, b_lo);
+  if (!beside) launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
+  fork_end(S, st, beside);
   return cudaGetLastError();
 }
 
@@ -793,6 +816,7 @@ __global__ void __launch_bounds__(C::NT) batch_step_kernel(const BatchLattice *l
         sS.koff = 0;
         sS.tm_g = sS.tm_u = nullptr;
         sS.err = err;
+        sS.fork = nullptr;
       }
     }
     __syncthreads();
@@ -812,7 +836,7 @@ static __global__ void batch_advance_kernel(BatchLattice *lats, int n) {
 template <class C>
 cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
                               int ne, const BatchTile *edge_lin, int nl, int *err, cudaStream_t st,
-                              const BatchFork *fork) {
+                              const StreamFork *fork) {
   // resident blocks of the persistent kernel on this device (computed once;
   // the initialisation of a function-local static is thread-safe)
   static const int blocks = [] {
@@ -823,20 +847,25 @@ cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *in
     return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }();
   // the frame tiles (few, long, latency-bound) run beside the interior tiles
-  // when a side stream is given: both read iteration k and write k + 1 of
-  // disjoint nodes; the counters advance once both have finished
-  const bool split = fork && ni > 0 && (ne > 0 || nl > 0);
-  cudaStream_t fs = st;
+  // when a side stream is given and the interior walk is short (beside a
+  // long persistent walk they would hold back blocks whose tiles are fixed):
+  // both read iteration k and write k + 1 of disjoint nodes; the counters
+  // advance once both have finished
+  const bool split = fork && ni > 0 && ni <= kForkWalk * blocks && (ne > 0 || nl > 0);
+  auto frame = [&](cudaStream_t fs) {
+    if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, err);
+    if (nl > 0)
+      batch_step_kernel<C, true, true><<<nl < blocks ? nl : blocks, C::NT, 0, fs>>>(lats, edge_lin, nl, err);
+  };
   if (split) {
     cudaEventRecord(fork->fork, st);
     cudaStreamWaitEvent(fork->side, fork->fork, 0);
-    fs = fork->side;
+    frame(fork->side);
   }
-  if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, err);
-  if (nl > 0) batch_step_kernel<C, true, true><<<nl < blocks ? nl : blocks, C::NT, 0, fs>>>(lats, edge_lin, nl, err);
   if (ni > 0) batch_step_kernel<C, false><<<ni < blocks ? ni : blocks, C::NT, 0, st>>>(lats, interior, ni, err);
+  if (!split) frame(st);
   if (split) {
-    cudaEventRecord(fork->join, fs);
+    cudaEventRecord(fork->join, fork->side);
     cudaStreamWaitEvent(st, fork->join, 0);
   }
   if (nlats > 0) batch_advance_kernel<<<(nlats + 127) / 128, 128, 0, st>>>(lats, nlats);
@@ -1027,13 +1056,15 @@ cudaError_t launch_step_tma(const Params &P, const StepPtrs &S, cudaStream_t st)
   int a_lo, a_hi, b_lo, b_hi;
   interior_range(P.nx, P.ny, C::TX, C::TY, a_lo, a_hi, b_lo, b_hi);
   const int ni = a_hi - a_lo, nj = b_hi - b_lo;
-  if (ni > 0 && nj > 0) {
-    if (!S.tm_g || !S.tm_u) return cudaErrorInvalidValue;
+  if (ni > 0 && nj > 0 && (!S.tm_g || !S.tm_u)) return cudaErrorInvalidValue;
+  const int nedge = ntx * nty - ni * nj;
+  const bool beside = fork_begin(S, st, ni > 0 && nj > 0 && nedge > 0);
+  if (beside) launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, S.fork->side);
+  if (ni > 0 && nj > 0)
     step_tma_kernel<C><<<dim3(ni, nj), C::NT, T::SMEM, st>>>(P, S, *(const CUtensorMap *)S.tm_g,
                                                                *(const CUtensorMap *)S.tm_u, a_lo, b_lo);
-  }
-  const int nedge = ntx * nty - ni * nj;
-  launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
+  if (!beside) launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
+  fork_end(S, st, beside);
   return cudaGetLastError();
 }
 
@@ -1199,23 +1230,30 @@ cudaError_t launch_step_tma2(const Params &P, const StepPtrs &S, cudaStream_t st
   int a_lo, a_hi, b_lo, b_hi;
   interior_range(P.nx, P.ny, C::TX, C::TY, a_lo, a_hi, b_lo, b_hi);
   const int ni = a_hi - a_lo, nj = b_hi - b_lo;
+  if (ni > 0 && nj > 0 && (!S.tm_g || !S.tm_u)) return cudaErrorInvalidValue;
+  // resident blocks (computed once, after the shared-memory opt-in that
+  // selecting the variant made; thread-safe initialisation)
+  static const int blocks = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_tma2_kernel<C>, C::NT, T2::SMEM);
+    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }();
+  const int ntiles = ni * nj;
+  // the frame kernel runs beside the interior one only while the walk is
+  // short: beside a long persistent walk it holds back blocks whose tiles are
+  // fixed (measured at 16384^2 with FP16 storage, 1150 tiles per block: 33
+  // instead of 60 GLUPS; at 4096 x 256, 4 tiles per block: 10 % faster)
+  const int nedge = ntx * nty - ni * nj;
+  const bool beside = fork_begin(S, st, ni > 0 && nj > 0 && nedge > 0 && ntiles <= kForkWalk * blocks);
+  if (beside) launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, S.fork->side);
   if (ni > 0 && nj > 0) {
-    if (!S.tm_g || !S.tm_u) return cudaErrorInvalidValue;
-    // resident blocks (computed once, after the shared-memory opt-in that
-    // selecting the variant made; thread-safe initialisation)
-    static const int blocks = [] {
-      int dev = 0, sms = 0, per = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_tma2_kernel<C>, C::NT, T2::SMEM);
-      return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
-    }();
-    const int ntiles = ni * nj;
     step_tma2_kernel<C><<<ntiles < blocks ? ntiles : blocks, C::NT, T2::SMEM, st>>>(
         P, S, *(const CUtensorMap *)S.tm_g, *(const CUtensorMap *)S.tm_u, a_lo, b_lo, ni, ntiles);
   }
-  const int nedge = ntx * nty - ni * nj;
-  launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
+  if (!beside) launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
+  fork_end(S, st, beside);
   return cudaGetLastError();
 }
 
@@ -1420,15 +1458,18 @@ cudaError_t launch_step_march(const Params &P, const StepPtrs &S, cudaStream_t s
   int a_lo, a_hi, b_lo, b_hi;
   interior_range(P.nx, P.ny, C::TX, C::TY, a_lo, a_hi, b_lo, b_hi);
   const int ni = a_hi - a_lo, nj = b_hi - b_lo;
+  if (ni > 0 && nj > 0 && (!S.tm_g || !S.tm_u)) return cudaErrorInvalidValue;
+  const int nedge = ntx * nty - ni * nj;
+  const bool beside = fork_begin(S, st, ni > 0 && nj > 0 && nedge > 0);
+  if (beside) launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, S.fork->side);
   if (ni > 0 && nj > 0) {
-    if (!S.tm_g || !S.tm_u) return cudaErrorInvalidValue;
     const int y_first = b_lo * C::TY, y_last = b_hi * C::TY;
     const int nseg = (y_last - y_first + M::SH - 1) / M::SH;
     step_march_kernel<C, M><<<ni * nseg, M::NT, M::SMEM, st>>>(P, S, *(const CUtensorMap *)S.tm_g,
                                                                *(const CUtensorMap *)S.tm_u, a_lo, ni, y_first, y_last);
   }
-  const int nedge = ntx * nty - ni * nj;
-  launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
+  if (!beside) launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
+  fork_end(S, st, beside);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,13 @@ struct Params {
   double inv_cs2;  // 1 / cs^2
 };
 
+// A second stream and two events with which one iteration runs its
+// frame-tile launches beside the interior-tile launch (fork, join).
+struct StreamFork {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+};
+
 // Device pointers of one lattice for one step: in/out buffers of the
 // distributions g (9 planes of ny*pitch), the displacement u (one record per
 // node) and the boundary side array (4 edges x blen x 4 entries of N = P + Pi(H)
@@ -51,6 +58,7 @@ struct StepPtrs {
   const void *tm_g;     // host pointers to the TMA descriptors of g_in and
   const void *tm_u;     //   u_in (TMA tile variants only)
   int *err;             // device flag set when a bounded wait gives up
+  const StreamFork *fork;  // host: run the frame tiles beside the interior tiles (or null)
 };
 
 struct TileShape {
@@ -71,12 +79,7 @@ struct BatchTile {
   int lat, a, b;
 };
 
-// A second stream and two events with which one batch iteration runs its
-// frame-tile launches beside the interior-tile launch (fork, join).
-struct BatchFork {
-  cudaStream_t side;
-  cudaEvent_t fork, join;
-};
+
 
 // Launchers, one set per precision (kernels_fp*.cu).  `variant` picks a tile
 // shape (0 = default).  Return a cudaError_t of the launch.
@@ -106,7 +109,7 @@ struct Launchers {
   // with the interior tiles; the counters advance after both)
   cudaError_t (*batch_step)(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
                             int ne, const BatchTile *edge_lin, int nl, int *err, cudaStream_t st,
-                            const BatchFork *fork);
+                            const StreamFork *fork);
   TileShape batch_tile;
   size_t g_elem, u_elem, b_elem;  // bytes per stored g value, per u record, per boundary entry
 };
@@ -163,6 +166,7 @@ struct lbs_handle {
   CUtensorMap tm_g[2];      // TMA descriptors of g[0], g[1] and u[0], u[1]
   CUtensorMap tm_u[2];      //   for the current variant (TMA variants only)
   bool tma;                 // the current variant stages tiles with TMA
+  lbs::StreamFork fork;     // side stream and events: frame tiles beside interior tiles
   lbs_lattice lat;          // the configuration the handle was created with
   lbs_material mat;
   lbs_bcs bcs;

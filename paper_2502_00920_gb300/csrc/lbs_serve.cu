@@ -60,7 +60,7 @@ struct lbs_server {
   lbs_server_stats st;
   // owned by the worker thread
   cudaStream_t stream = nullptr;
-  lbs::BatchFork fork = {nullptr, nullptr, nullptr};  // frame tiles beside interior tiles
+  lbs::StreamFork fork = {nullptr, nullptr, nullptr};  // frame tiles beside interior tiles
   BatchLattice *d_lats = nullptr;
   int lat_cap = 0;
   BatchTile *d_tiles = nullptr;
