@@ -464,7 +464,9 @@ __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *_
 #pragma unroll
     for (int q = 1; q < 9; ++q) g0[q] = gload(g, q * plane + idx, inv);
     g0[0] = 0;
-  } else {
+  } else if constexpr (sizeof(R) == 8) {
+    // FP64: loads between the branches (the batched form below takes the
+    // frame kernel past 128 registers, halving its blocks per SM)
     unsigned mask = 0;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -486,6 +488,36 @@ __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *_
         f[q] = gload(g, q * plane + (size_t)sy * P.pitch + sx, inv);
       }
     }
+    if (mask) wall_rules<R, typename Pr::gs, LIN>(P, bnd, g, sev, x, y, g0, mask, f, gsc);
+  } else {
+    // source of each population first (the node itself where the source
+    // lies outside the lattice), then all eighteen loads without branches in
+    // between, so that they are in flight together
+    unsigned mask = 0;
+    size_t src[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      int sx = x - ex(q), sy = y - ey(q);
+      bool out = false;
+      if (sx < 0 || sx >= P.nx) {
+        if (P.per_x) sx = sx < 0 ? sx + P.nx : sx - P.nx;
+        else out = true;
+      }
+      if (sy < 0 || sy >= P.ny) {
+        if (P.per_y) sy = sy < 0 ? sy + P.ny : sy - P.ny;
+        else out = true;
+      }
+      if (out) mask |= 1u << q;
+      src[q] = out ? idx : (size_t)sy * P.pitch + sx;
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      g0[q] = gload(g, q * plane + idx, inv);
+      f[q] = gload(g, q * plane + src[q], inv);
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      if (mask & (1u << q)) f[q] = 0;
     if (mask) wall_rules<R, typename Pr::gs, LIN>(P, bnd, g, sev, x, y, g0, mask, f, gsc);
   }
   gx = (g0[1] - g0[3]) + (g0[5] - g0[6]) + (g0[8] - g0[7]);
