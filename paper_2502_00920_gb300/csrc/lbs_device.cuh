@@ -745,12 +745,29 @@ __host__ __device__ inline void edge_tile(int e, int ntx, int a_lo, int a_hi, in
   b = b_hi + e / ntx;
 }
 
-template <class C, bool LIN>
-__global__ void __launch_bounds__(C::NT) step_edge_kernel(const Params P, const StepPtrs S, int ntx, int a_lo, int a_hi,
-                                                          int b_lo, int b_hi) {
+// With SPLIT, a frame tile is processed as two half-height tiles by two
+// blocks (one node per thread fewer in each).  On a small lattice the frame
+// tiles are few and the iteration waits on their latency; once there are
+// more of them than SMs the halves' extra halo work costs more than it saves
+// (launch_edge chooses).
+template <class C, bool SPLIT>
+struct FrameCfg {
+  using type = C;
+};
+template <class C>
+struct FrameCfg<C, true> {
+  using type = Cfg<typename C::PrT, C::TX, C::TY / 2, C::NTY>;
+};
+
+template <class C, bool LIN, bool SPLIT = false>
+__global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) step_edge_kernel(const Params P, const StepPtrs S,
+                                                                                 int ntx, int a_lo, int a_hi,
+                                                                                 int b_lo, int b_hi) {
+  using H = typename FrameCfg<C, SPLIT>::type;
+  constexpr int parts = C::TY / H::TY;
   int a, b;
-  edge_tile(blockIdx.x, ntx, a_lo, a_hi, b_lo, b_hi, a, b);
-  step_tile<C, true, LIN>(P, S, a * C::TX, b * C::TY);
+  edge_tile(blockIdx.x / parts, ntx, a_lo, a_hi, b_lo, b_hi, a, b);
+  step_tile<H, true, LIN>(P, S, a * C::TX, b * C::TY + (blockIdx.x % parts) * H::TY);
 }
 
 // the frame tiles of one iteration; the two-point wall extrapolation has its
@@ -759,6 +776,20 @@ template <class C>
 void launch_edge(const Params &P, const StepPtrs &S, int nedge, int ntx, int a_lo, int a_hi, int b_lo, int b_hi,
                  cudaStream_t st) {
   if (nedge <= 0) return;
+  if constexpr (C::CPT % 2 == 0) {
+    static const int sms = [] {
+      int dev = 0, n = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+      return n > 0 ? n : 1;
+    }();
+    if (nedge <= sms) {
+      using H = typename FrameCfg<C, true>::type;
+      if (P.extrap) step_edge_kernel<C, true, true><<<2 * nedge, H::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+      else step_edge_kernel<C, false, true><<<2 * nedge, H::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+      return;
+    }
+  }
   if (P.extrap) step_edge_kernel<C, true><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
   else step_edge_kernel<C, false><<<nedge, C::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
 }
