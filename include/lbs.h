@@ -177,15 +177,16 @@ int lbs_fields(lbs_handle *h, double *u, double *v, double *P);
 /* As lbs_fields into caller-owned DEVICE buffers; asynchronous. */
 int lbs_fields_device(lbs_handle *h, double *u, double *v, double *P);
 
-/* As lbs_fields, but without allocating device memory.  (The paper has no
+/* As lbs_fields, but never allocating device memory.  (The paper has no
  * counterpart; this is a property of the library.)  lbs_fields stages the
- * output in device temporaries the size of the whole lattice, allocated and
- * freed on every call.  Some callers cannot do that: a process whose device
- * memory is already taken (a server whose resident lattices fill its HBM
- * budget, or a framework's caching allocator holding most of the free
- * memory) would get LBS_ENOMEM for exactly the large lattices whose results
- * matter, and a caller with a latency budget cannot afford cudaFree, which
- * waits for the whole device.  This entry point instead copies the fields
+ * output in the handle's idle state buffers and allocates a device
+ * temporary the size of the lattice for a field that does not fit there
+ * (P under LBS_FP16S).  Some callers cannot allow even that: a process
+ * whose device memory is already taken (a server whose resident lattices
+ * fill its HBM budget, or a framework's caching allocator holding most of
+ * the free memory) would get LBS_ENOMEM for exactly the large lattices whose
+ * results matter, and a caller with a latency budget cannot afford cudaFree,
+ * which waits for the whole device.  This entry point instead copies the fields
  * out a block of rows at a time through one fixed staging array of 8 MiB
  * (2^20 doubles) in device memory, a file-scope static that every GPU which
  * loads the library holds until the process exits.  It calls no cudaMalloc

@@ -1,10 +1,11 @@
 // lbs_fields_static: field output without device allocation.
 //
-// lbs_fields stages u, v and P in device temporaries the size of the whole
-// lattice (cudaMalloc / cudaFree on every call; up to 17 GB for a 16384^2
-// lattice).  This variant stages them through one fixed 8 MiB array in device
-// memory, a row block at a time, so a call allocates nothing.  The kernel is a
-// variant of the field-output kernel that writes only the rows of one block.
+// lbs_fields stages u, v and P in the handle's idle state buffers, whole
+// fields at a time, and allocates a device temporary for a field that fits
+// nowhere there (P under FP16 storage: 8.6 GB for a 16384^2 lattice).  This
+// variant stages them through one fixed 8 MiB array in device memory, a row
+// block at a time, so a call never allocates.  The kernel is a variant of the
+// field-output kernel that writes only the rows of one block.
 #include <mutex>
 
 #include "lbs_device.cuh"
