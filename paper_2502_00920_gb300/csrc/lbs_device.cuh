@@ -855,15 +855,19 @@ cudaError_t launch_step(const Params &P, const StepPtrs &S, cudaStream_t st) {
 // different sizes: block i takes tiles i, i + grid, ...  Each tile runs the
 // same step_tile code as the single-lattice kernels, on its lattice's buffers
 // chosen by the parity of that lattice's iteration counter.
-template <class C, bool EDGE, bool LIN = false>
-__global__ void __launch_bounds__(C::NT) batch_step_kernel(const BatchLattice *lats, const BatchTile *tiles, int ntiles,
-                                                           int *err) {
+// SPLIT (frame tiles only): each table tile is run as two half-height tiles.
+template <class C, bool EDGE, bool LIN = false, bool SPLIT = false>
+__global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) batch_step_kernel(const BatchLattice *lats,
+                                                                                  const BatchTile *tiles, int ntiles,
+                                                                                  int *err) {
+  using H = typename FrameCfg<C, SPLIT>::type;
+  constexpr int parts = C::TY / H::TY;
   __shared__ Params sP;
   __shared__ StepPtrs sS;
   __shared__ int skip;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (int t = blockIdx.x; t < ntiles * parts; t += gridDim.x) {
     if (threadIdx.x == 0) {
-      const BatchTile T = tiles[t];
+      const BatchTile T = tiles[t / parts];
       const BatchLattice &L = lats[T.lat];
       skip = L.k >= L.kend;
       if (!skip) {
@@ -884,8 +888,8 @@ __global__ void __launch_bounds__(C::NT) batch_step_kernel(const BatchLattice *l
     }
     __syncthreads();
     if (!skip) {
-      const BatchTile T = tiles[t];
-      step_tile<C, EDGE, LIN>(sP, sS, T.a * C::TX, T.b * C::TY);
+      const BatchTile T = tiles[t / parts];
+      step_tile<H, EDGE, LIN>(sP, sS, T.a * C::TX, T.b * C::TY + (t % parts) * H::TY);
     }
     __syncthreads();  // the next tile reuses the shared memory
   }
@@ -915,7 +919,23 @@ cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *in
   // both read iteration k and write k + 1 of disjoint nodes; the counters
   // advance once both have finished
   const bool split = fork && ni > 0 && ni <= kForkWalk * blocks && (ne > 0 || nl > 0);
+  // no more frame tiles than SMs: run each as two half-height blocks (the
+  // frame launch is then the iteration's critical path)
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
   auto frame = [&](cudaStream_t fs) {
+    if constexpr (C::CPT % 2 == 0) {
+      if (ne + nl <= sms) {
+        using H = typename FrameCfg<C, true>::type;
+        if (ne > 0) batch_step_kernel<C, true, false, true><<<2 * ne, H::NT, 0, fs>>>(lats, edge, ne, err);
+        if (nl > 0) batch_step_kernel<C, true, true, true><<<2 * nl, H::NT, 0, fs>>>(lats, edge_lin, nl, err);
+        return;
+      }
+    }
     if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, err);
     if (nl > 0)
       batch_step_kernel<C, true, true><<<nl < blocks ? nl : blocks, C::NT, 0, fs>>>(lats, edge_lin, nl, err);
