@@ -111,3 +111,17 @@ def test_tile_variants_listed(L):
     for prec in ("fp64", "fp32", "fp16s"):
         v = L.tile_variants(prec)
         assert len(v) >= 2 and all(tx % 32 == 0 and ty > 0 for tx, ty in v)
+
+
+def test_no_gpu_means_an_error_not_a_fallback(L):
+    """Without a CUDA device a valid configuration is refused with LBS_ECUDA:
+    the library has no CPU path to fall back to, and null handles are
+    rejected before any device call."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(L.LbsError) as e:
+        L.Simulation(I.tension(32, 32, 10, ramp=5, model="nh", precision="fp32"))
+    assert e.value.code == L.ECUDA
+    assert L.lib().lbs_step(None, 1) == L.EINVAL
+    assert L.lib().lbs_fields(None, None, None, None) == L.EINVAL
