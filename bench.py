@@ -134,13 +134,18 @@ def oracle_rate(n: int, target_s: float, seed: int = 5):
                       f"({dt:.1f} s) after 1 untimed"}, steps, dt
 
 
+L2_BYTES = 129 * 1024 * 1024  # GB300 L2
+
+
 def arm_config(n: int, precision: str, world: int) -> dict:
     """The workload both arms report on: the roofline lattice."""
     bpn = BYTES_PER_NODE[precision]
+    state = bpn * n * n  # both buffers of g and u
+    l2 = (f"state {state / 1e9:.1f} GB per lattice, larger than L2 (no flush needed)" if state > L2_BYTES else
+          f"state {state / 1e6:.1f} MB per lattice, fits in L2 (not flushed: a small-lattice run, not a bench value)")
     return {"workload": f"roofline {n}x{n} periodic neo-Hooke, random initial velocity",
             "nx": n, "ny": n, "model": "nh", "E": 1.0, "nu": 0.3, "tau": 0.55,
-            "precision": precision, "parallelism": f"replicas x{world}",
-            "l2": f"state {bpn * n * n / 1e9:.1f} GB per lattice, larger than L2 (no flush needed)"}
+            "precision": precision, "parallelism": f"replicas x{world}", "l2": l2}
 
 
 def run_reference(args, rank: int, world: int):
