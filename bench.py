@@ -510,16 +510,29 @@ def suite_cantilever(args, L, I, O, emit, gpu_run, rel):
 def suite_paper(args, L, I, O, emit, gpu_run, rel):
     # the paper's examples at its own sizes against the oracle over their
     # horizons, and a refinement ladder (self-convergence on the GPU, FP64)
+    # the bending wave at each relaxation time of the paper's sweep; besides
+    # parity, how far each tau moves u from tau = 0.55 (the paper compares
+    # each against FE data, which is not available here)
+    u_wave = {}
     for name, case, T in (("paper_tension_nh_0.3", I.paper_tension("nh", 0.3), 2.2),
                           ("paper_shear_svk_0.2", I.paper_shear("svk", 0.2), 2.2),
-                          ("paper_wave_tau0.55", I.paper_wave(0.55), 12.0)):
+                          ("paper_wave_tau0.54", I.paper_wave(0.54), 12.0),
+                          ("paper_wave_tau0.55", I.paper_wave(0.55), 12.0),
+                          ("paper_wave_tau0.57", I.paper_wave(0.57), 12.0),
+                          ("paper_wave_tau0.59", I.paper_wave(0.59), 12.0)):
         steps = int(round(T / O.params(case)["dt"]))
         (u, v, P), dt, unstable, _ = gpu_run(case, steps)
         o = O.OracleSim(case)
         o.step(steps)
         ur, vr, Pr = o.fields()
-        emit(config=name, precision="fp64", nx=case.nx, ny=case.ny, iterations=steps, unstable_gpu=unstable,
-             u_err=rel(u, ur), v_err=rel(v, vr), P_err=rel(P, Pr), max_abs_u=float(np.abs(ur).max()))
+        row = dict(config=name, precision="fp64", nx=case.nx, ny=case.ny, iterations=steps, unstable_gpu=unstable,
+                   u_err=rel(u, ur), v_err=rel(v, vr), P_err=rel(P, Pr), max_abs_u=float(np.abs(ur).max()))
+        if name.startswith("paper_wave"):
+            u_wave[case.tau] = u
+        emit(**row)
+    if 0.55 in u_wave:
+        emit(config="paper_wave_tau_sweep", precision="fp64", t=12.0,
+             u_change_vs_tau055={str(t): rel(u, u_wave[0.55]) for t, u in u_wave.items() if t != 0.55})
     for name, mk in (("tension_nh_0.3", lambda n: I.paper_tension("nh", 0.3, n=n)),
                      ("shear_svk_0.2", lambda n: I.paper_shear("svk", 0.2, n=n))):
         c20 = mk(20)

@@ -349,13 +349,16 @@ def test_tension_32_full_history(L, oracle_mod):
 
 def paper_cases():
     """The paper's own examples at its lattice sizes (Sect. 4): 40 x 40
-    tension and shear to t = 2.2, the 160 x 40 bending wave to t = 12."""
+    tension and shear to t = 2.2, the 160 x 40 bending wave to t = 12 at each
+    relaxation time of the paper's sweep (0.54, 0.55, 0.57, 0.59)."""
     return {
         "paper_tension_nh_0.3": (I.paper_tension("nh", 0.3), 2.2),
         "paper_tension_svk_0.25": (I.paper_tension("svk", 0.25), 2.2),
         "paper_shear_nh_0.3": (I.paper_shear("nh", 0.3), 2.2),
         "paper_shear_svk_0.2": (I.paper_shear("svk", 0.2), 2.2),
+        "paper_wave_tau0.54": (I.paper_wave(0.54), 12.0),
         "paper_wave_tau0.55": (I.paper_wave(0.55), 12.0),
+        "paper_wave_tau0.57": (I.paper_wave(0.57), 12.0),
         "paper_wave_tau0.59": (I.paper_wave(0.59), 12.0),
     }
 
