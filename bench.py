@@ -113,6 +113,17 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def oracle_config_rate(O, case, steps: int) -> dict:
+    """The oracle timed on one workload configuration (all host cores):
+    `steps` iterations from the configuration's initial state."""
+    sim = O.OracleSim(case.replace(precision="fp64"))
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    return {"oracle_mlups": case.nx * case.ny * steps / dt / 1e6, "oracle_cores": O.OracleSim.threads(),
+            "oracle_sample": f"{steps} iterations from the initial state ({dt:.1f} s)"}
+
+
 def oracle_rate(n: int, target_s: float, seed: int = 5):
     """MLUPS of the CPU oracle on a bounded sample of the workload: the same
     recipe (periodic neo-Hooke, seeded random velocity) on an n x n lattice,
@@ -432,7 +443,7 @@ def suite(args):
 def suite_tension(args, L, I, O, emit, gpu_run, rel, first_nonfinite_gpu, first_nonfinite_oracle):
     case = I.tension()
     emit(config="tension_32x32_nh", first_nonfinite_oracle=first_nonfinite_oracle(case, 2000)[0],
-         first_nonfinite_gpu_fp64=first_nonfinite_gpu(case, 2000))
+         first_nonfinite_gpu_fp64=first_nonfinite_gpu(case, 2000), **oracle_config_rate(O, case, 1000))
     ora = O.OracleSim(case)
     ora_hist, k_nan = {}, None
     for k in range(0, 2000, 50):
@@ -460,8 +471,9 @@ def suite_shear(args, L, I, O, emit, gpu_run, rel, first_nonfinite_gpu, first_no
     for nu in (0.0, 0.1, 0.2, 0.3, 0.4, 0.45):
         case = I.shear(256, nsh, model="svk", nu=nu)
         k_o, fo = first_nonfinite_oracle(case, nsh)
+        extra = oracle_config_rate(O, case, 500) if nu == 0.2 else {}
         emit(config="shear_256_svk", nu=nu, first_nonfinite_oracle=k_o,
-             first_nonfinite_gpu_fp64=first_nonfinite_gpu(case, nsh))
+             first_nonfinite_gpu_fp64=first_nonfinite_gpu(case, nsh), **extra)
         for prec in ("fp64", "fp32", "fp16s"):
             (u, v, P), dt, unstable, _ = gpu_run(case.replace(precision=prec), nsh, monitor=1000)
             fin = fo is not None and np.isfinite(u).all()
@@ -498,13 +510,17 @@ def suite_cantilever(args, L, I, O, emit, gpu_run, rel):
                 row["u_err_vs_fp64"] = rel(u, ref["fp64"][0])
         emit(**row)
     o = O.OracleSim(case.replace(precision="fp64"))
+    t0 = time.perf_counter()
     o.step(args.suite_cantilever_prefix)
+    t_ora = time.perf_counter() - t0
     with L.Simulation(case.replace(precision="fp64")) as s:
         s.step(args.suite_cantilever_prefix)
         s.sync()
         ug = s.fields()[0]
     emit(config="cantilever_4096x256", precision="fp64", iterations=args.suite_cantilever_prefix,
-         u_err_vs_oracle=rel(ug, o.fields()[0]))
+         u_err_vs_oracle=rel(ug, o.fields()[0]),
+         oracle_mlups=4096 * 256 * args.suite_cantilever_prefix / t_ora / 1e6, oracle_cores=O.OracleSim.threads(),
+         oracle_sample=f"{args.suite_cantilever_prefix} iterations from the initial state ({t_ora:.1f} s)")
 
 
 def suite_paper(args, L, I, O, emit, gpu_run, rel):
@@ -523,10 +539,14 @@ def suite_paper(args, L, I, O, emit, gpu_run, rel):
         steps = int(round(T / O.params(case)["dt"]))
         (u, v, P), dt, unstable, _ = gpu_run(case, steps)
         o = O.OracleSim(case)
+        t0 = time.perf_counter()
         o.step(steps)
+        t_ora = time.perf_counter() - t0
         ur, vr, Pr = o.fields()
         row = dict(config=name, precision="fp64", nx=case.nx, ny=case.ny, iterations=steps, unstable_gpu=unstable,
-                   u_err=rel(u, ur), v_err=rel(v, vr), P_err=rel(P, Pr), max_abs_u=float(np.abs(ur).max()))
+                   u_err=rel(u, ur), v_err=rel(v, vr), P_err=rel(P, Pr), max_abs_u=float(np.abs(ur).max()),
+                   gpu_mlups=case.nx * case.ny * steps / dt / 1e6,
+                   oracle_mlups=case.nx * case.ny * steps / t_ora / 1e6, oracle_cores=O.OracleSim.threads())
         if name.startswith("paper_wave"):
             u_wave[case.tau] = u
         emit(**row)
@@ -565,6 +585,8 @@ def suite_roofline(args, L, I, torch, dev, emit):
         emit(config="roofline_16384", precision=prec, **r)
         del u
         torch.cuda.empty_cache()
+    cpu = oracle_rate(1024, 10.0)[0]
+    emit(config="roofline_16384", oracle_mlups=cpu["value"], oracle_cores=cpu["cores"], oracle_sample=cpu["sample"])
 
 
 def main():
