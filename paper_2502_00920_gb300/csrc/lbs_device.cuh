@@ -745,10 +745,10 @@ __host__ __device__ inline void edge_tile(int e, int ntx, int a_lo, int a_hi, in
   b = b_hi + e / ntx;
 }
 
-// With SPLIT, a frame tile is processed as two half-height tiles by two
-// blocks (one node per thread fewer in each).  On a small lattice the frame
+// With SPLIT, a frame tile of CPT nodes per thread is processed as CPT
+// tiles of one node per thread by CPT blocks.  On a small lattice the frame
 // tiles are few and the iteration waits on their latency; once there are
-// more of them than SMs the halves' extra halo work costs more than it saves
+// more of them than SMs the pieces' extra halo work costs more than it saves
 // (launch_edge chooses).
 template <class C, bool SPLIT>
 struct FrameCfg {
@@ -756,7 +756,7 @@ struct FrameCfg {
 };
 template <class C>
 struct FrameCfg<C, true> {
-  using type = Cfg<typename C::PrT, C::TX, C::TY / 2, C::NTY>;
+  using type = Cfg<typename C::PrT, C::TX, C::NTY, C::NTY>;
 };
 
 template <class C, bool LIN, bool SPLIT = false>
@@ -776,7 +776,7 @@ template <class C>
 void launch_edge(const Params &P, const StepPtrs &S, int nedge, int ntx, int a_lo, int a_hi, int b_lo, int b_hi,
                  cudaStream_t st) {
   if (nedge <= 0) return;
-  if constexpr (C::CPT % 2 == 0) {
+  if constexpr (C::CPT >= 2) {
     static const int sms = [] {
       int dev = 0, n = 0;
       cudaGetDevice(&dev);
@@ -785,8 +785,9 @@ void launch_edge(const Params &P, const StepPtrs &S, int nedge, int ntx, int a_l
     }();
     if (nedge <= sms) {
       using H = typename FrameCfg<C, true>::type;
-      if (P.extrap) step_edge_kernel<C, true, true><<<2 * nedge, H::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
-      else step_edge_kernel<C, false, true><<<2 * nedge, H::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+      const int nb = C::CPT * nedge;
+      if (P.extrap) step_edge_kernel<C, true, true><<<nb, H::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+      else step_edge_kernel<C, false, true><<<nb, H::NT, 0, st>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
       return;
     }
   }
@@ -855,7 +856,8 @@ cudaError_t launch_step(const Params &P, const StepPtrs &S, cudaStream_t st) {
 // different sizes: block i takes tiles i, i + grid, ...  Each tile runs the
 // same step_tile code as the single-lattice kernels, on its lattice's buffers
 // chosen by the parity of that lattice's iteration counter.
-// SPLIT (frame tiles only): each table tile is run as two half-height tiles.
+// SPLIT (frame tiles only): each table tile is run as CPT tiles of one node
+// per thread.
 template <class C, bool EDGE, bool LIN = false, bool SPLIT = false>
 __global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) batch_step_kernel(const BatchLattice *lats,
                                                                                   const BatchTile *tiles, int ntiles,
@@ -919,8 +921,8 @@ cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *in
   // both read iteration k and write k + 1 of disjoint nodes; the counters
   // advance once both have finished
   const bool split = fork && ni > 0 && ni <= kForkWalk * blocks && (ne > 0 || nl > 0);
-  // no more frame tiles than SMs: run each as two half-height blocks (the
-  // frame launch is then the iteration's critical path)
+  // no more frame tiles than SMs: run each as CPT blocks of one node per
+  // thread (the frame launch is then the iteration's critical path)
   static const int sms = [] {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -928,11 +930,11 @@ cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *in
     return n > 0 ? n : 1;
   }();
   auto frame = [&](cudaStream_t fs) {
-    if constexpr (C::CPT % 2 == 0) {
+    if constexpr (C::CPT >= 2) {
       if (ne + nl <= sms) {
         using H = typename FrameCfg<C, true>::type;
-        if (ne > 0) batch_step_kernel<C, true, false, true><<<2 * ne, H::NT, 0, fs>>>(lats, edge, ne, err);
-        if (nl > 0) batch_step_kernel<C, true, true, true><<<2 * nl, H::NT, 0, fs>>>(lats, edge_lin, nl, err);
+        if (ne > 0) batch_step_kernel<C, true, false, true><<<C::CPT * ne, H::NT, 0, fs>>>(lats, edge, ne, err);
+        if (nl > 0) batch_step_kernel<C, true, true, true><<<C::CPT * nl, H::NT, 0, fs>>>(lats, edge_lin, nl, err);
         return;
       }
     }
