@@ -178,3 +178,23 @@ def test_preemption_setting_is_validated(L):
     with pytest.raises(L.LbsError) as e:
         L.Server(precision="fp32", preempt_after_s=-1.0)
     assert e.value.code == L.EINVAL
+
+
+def test_zero_iteration_requests_and_steps(L):
+    """Empty work: a request of zero iterations, alone or beside others,
+    returns its initial state, and lbs_step(h, 0) changes nothing."""
+    c0 = I.tension(48, 40, 0, ramp=50, model="nh", nu=0.2, precision="fp32")
+    other = I.tension(64, 48, 120, ramp=50, model="svk", nu=0.1, precision="fp32")
+    with L.Simulation(c0) as s:
+        ref = s.fields()
+        s.step(0)
+        s.sync()
+        assert s.iteration == 0
+        assert all(np.array_equal(a, b) for a, b in zip(s.fields(), ref))
+    for batch in ([c0], [c0, other]):
+        with L.Server(precision="fp32", chunk=32) as srv:
+            tickets = [srv.submit(c) for c in batch]
+            srv.drain(60)
+            u, v, P, rc = srv.result(tickets[0])
+            assert rc == L.OK and all(srv.result(t)[3] == L.OK for t in tickets[1:])
+        assert np.array_equal(u, ref[0]) and np.array_equal(v, ref[1]) and np.array_equal(P, ref[2])
