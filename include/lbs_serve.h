@@ -27,7 +27,8 @@
  * back; on re-admission it resumes from that state (lbs_load), so its result
  * is bitwise the one it would have had without the interruption.  Nothing is
  * swapped out unless the waiting request then fits.
- * Each lattice computes exactly what lbs_step computes for it alone.
+ * Each lattice computes exactly what lbs_step computes for it alone, with
+ * either wall reading (lbs_lattice.wall_extrap) and any mix of the two.
  *
  * The server owns its device memory and its results until lbs_result hands
  * them over.  All functions are thread-safe.
