@@ -286,7 +286,9 @@ size_t lbs_footprint(const lbs_lattice *lat);
 int lbs_constitutive(int32_t model, double lam, double mu, const double H[4], double P[4], double N[4]);
 
 /* Number of tile variants compiled for a precision, and their shapes
- * (cells along x and y per thread block). */
+ * (cells along x and y per thread block).  tx and ty (caller-owned) receive
+ * *count entries each; pass NULL for both to learn the count first.
+ * Errors: LBS_EINVAL for an unknown precision. */
 int lbs_tile_variants(int32_t precision, int32_t *count, int32_t *tx, int32_t *ty);
 
 /* 1 if a tile variant stages its interior tiles in shared memory with TMA
