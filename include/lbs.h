@@ -308,7 +308,8 @@ const char *lbs_tile_variant_name(int32_t precision, int32_t variant);
  * scratch lattice with the same material, edges and precision and at most
  * 4096 x 4096 nodes (direct launches, CUDA events, `steps` iterations after
  * two untimed ones) and return the fastest in *best.  ms, if not NULL,
- * receives the time per iteration of each variant.  Results are cached per
+ * receives the time per iteration of each variant (caller-owned, as many
+ * entries as lbs_tile_variants reports for the precision).  Results are cached per
  * (nx, ny, precision, model, periodic axes) for the life of the process;
  * a cached configuration is not timed again.  Allocates a scratch lattice. */
 int lbs_autotune(const lbs_lattice *lat, const lbs_material *mat, const lbs_bcs *bcs, int32_t steps, int32_t *best,
