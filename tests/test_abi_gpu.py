@@ -196,3 +196,29 @@ def test_host_transfers_staged_in_the_idle_buffers(L, precision):
         s.step(60)
         s.sync()
         assert all(np.array_equal(a, b) for a, b in zip(s.fields(), ref_end))
+
+
+def test_separate_handles_on_separate_threads(L):
+    """Handles are independent: four lattices stepped at once from four host
+    threads (each handle on its own streams) give the bits they give when run
+    one after another."""
+    import threading
+    cases = [case(p, nx=96 + 17 * i, ny=64 + 9 * i) for i, p in enumerate(["fp32", "fp16s", "fp64", "fp32"])]
+    ref = [run(L, c, steps=150) for c in cases]
+    out = [None] * len(cases)
+    errors = []
+
+    def work(i):
+        try:
+            out[i] = run(L, cases[i], steps=150)
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(cases))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(120)
+    assert not errors, errors
+    for got, want in zip(out, ref):
+        assert same(got, want)
