@@ -100,7 +100,8 @@ def test_invalid_configurations_are_rejected(L):
     bad = [I.Case("b", 2, 8, 0), I.Case("b", 8, 8, 0, tau=0.5), I.Case("b", 8, 8, 0, nu=0.5),
            I.Case("b", 8, 8, 0, edges=(I.PERIODIC, I.FREE, I.FREE, I.FREE)),
            I.Case("b", 8, 8, 0, edges=(I.Edge("neumann", "disp_ramp", (1, 0), 0, 10),) + (I.FREE,) * 3),
-           I.Case("b", 8, 8, 0, edges=(I.Edge("neumann", "linear_ramp", (1, 0), 5, 5),) + (I.FREE,) * 3)]
+           I.Case("b", 8, 8, 0, edges=(I.Edge("neumann", "linear_ramp", (1, 0), 5, 5),) + (I.FREE,) * 3),
+           I.Case("b", 200000, 200000, 0)]  # more than 2^34 nodes
     for c in bad:
         with pytest.raises(L.LbsError) as e:
             L.Simulation(c)
