@@ -33,8 +33,9 @@
  *       i.e. computed in block 3 of the previous iteration (or at initialisation).
  *       ORA_EXTRAP_LINEAR selects the other reading: v + (v - v_in)/2 for each
  *       wall the link crosses, v_in at the next node inwards (the wall lies half
- *       a spacing beyond the node).  Its pins are the uniform-state, symmetry
- *       and linearity tests; the factor 1/2 itself is parity unpinned.
+ *       a spacing beyond the node).  Pinned through ora_wall_value: on a field
+ *       that is linear across the wall the carried value is the field at the
+ *       wall itself (x = -dX/2 from the boundary node), exactly.
  *   R8  corners: each outgoing link takes the rule of the wall it crosses,
  *       with the Pi* of that wall (its other diagonal entry from the node's
  *       own moment); a diagonal link crossing two walls is Dirichlet if either
@@ -351,6 +352,20 @@ static double at_wall(const ora_sim *s, const double *a, int x, int y, int wx, i
   if (wx >= 0) e += 0.5 * (v - a[node(s, wx == ORA_LEFT ? x + 1 : x - 1, y)]);
   if (wy >= 0) e += 0.5 * (v - a[node(s, x, wy == ORA_BOTTOM ? y + 1 : y - 1)]);
   return e;
+}
+
+/* the building block above on a caller's scalar field a[ny][nx], for the pin
+ * tests; NAN if (x, y) does not lie on the named walls */
+double ora_wall_value(const ora_config *cfg, const double *a, int x, int y, int wx, int wy) {
+  if (x < 0 || x >= cfg->nx || y < 0 || y >= cfg->ny) return NAN;
+  int okx = wx == -1 || (wx == ORA_LEFT && x == 0) || (wx == ORA_RIGHT && x == cfg->nx - 1);
+  int oky = wy == -1 || (wy == ORA_BOTTOM && y == 0) || (wy == ORA_TOP && y == cfg->ny - 1);
+  if (!okx || !oky) return NAN;
+  ora_sim tmp;
+  memset(&tmp, 0, sizeof(tmp));
+  tmp.cfg = *cfg;
+  tmp.n = (long)cfg->nx * cfg->ny;
+  return at_wall(&tmp, a, x, y, wx, wy);
 }
 
 static void wall_flux_column(const ora_sim *s, int x, int y, int edge, int wx, int wy, double col[2]) {

@@ -96,6 +96,11 @@ void ora_equilibrium(double cs, double r, const double j[2], const double Pi[4],
 void ora_forcing(double cs, const double S[2], double psi[9]);
 void ora_gradient(const ora_config *cfg, const double *u, double *H);
 void ora_load(const ora_config *cfg, int edge, long k, double out[2]);
+/* A node value a[y*nx + x] carried to the wall(s) (wx: ORA_LEFT/ORA_RIGHT or
+ * -1, wy: ORA_BOTTOM/ORA_TOP or -1) a boundary link crosses, as the Neumann
+ * rule of Sect. 3.3 takes r, the Pi entries and P + Pi(H) under cfg->extrap;
+ * NAN if (x, y) is not on those walls. */
+double ora_wall_value(const ora_config *cfg, const double *a, int x, int y, int wx, int wy);
 
 #ifdef __cplusplus
 }

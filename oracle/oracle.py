@@ -75,6 +75,9 @@ def lib():
         L.ora_forcing.argtypes = [ctypes.c_double, _dp, _dp]
         L.ora_gradient.argtypes = [ctypes.POINTER(_Config), _dp, _dp]
         L.ora_load.argtypes = [ctypes.POINTER(_Config), ctypes.c_int, ctypes.c_long, _dp]
+        L.ora_wall_value.restype = ctypes.c_double
+        L.ora_wall_value.argtypes = [ctypes.POINTER(_Config), _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int]
         _LIB = L
     return _LIB
 
@@ -204,3 +207,14 @@ def load(case, edge: int, k: int) -> np.ndarray:
     out = np.empty(2)
     lib().ora_load(ctypes.byref(config(case)), int(edge), int(k), _ptr(out))
     return out
+
+
+WALL = {None: -1, "left": 0, "right": 1, "bottom": 2, "top": 3}
+
+
+def wall_value(case, a, x: int, y: int, xwall=None, ywall=None) -> float:
+    """The oracle's value of the scalar node field a[ny, nx] at node (x, y)
+    carried to the named walls, as its Neumann rule does (case.extrap)."""
+    a = _f64(a, (case.ny, case.nx))
+    return float(lib().ora_wall_value(ctypes.byref(config(case)), _ptr(a), int(x), int(y), WALL[xwall],
+                                      WALL[ywall]))

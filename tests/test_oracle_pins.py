@@ -534,3 +534,42 @@ def test_homogeneous_stress_under_its_traction_is_static(oracle_mod, model, extr
     assert np.abs(u - u0).max() <= 1e-13
     assert np.abs(v).max() <= 1e-13
     assert np.abs(Pf - P.reshape(4)).max() <= 1e-13
+
+
+@pytest.mark.parametrize("xwall,ywall", [("left", None), ("right", None), (None, "bottom"), (None, "top"),
+                                         ("left", "bottom"), ("right", "bottom"), ("left", "top"),
+                                         ("right", "top")])
+def test_linear_wall_value_is_the_field_at_the_wall(oracle_mod, xwall, ywall):
+    """Pins the coefficient of the two-point reading of "extrapolated to the
+    boundary" (Sect. 3.3): the wall lies half a spacing beyond the boundary
+    node, so for a field that is linear across it the carried value must be
+    the field at the wall position exactly (at a corner, at the corner point
+    half a spacing out along both normals).  The expected value is the
+    linear field evaluated at that point, not the extrapolation formula; a
+    coefficient of 0, 1/4 or 1 (checked below to give another number), or an
+    inner node taken from the wrong side, fails it.  The node's own value
+    (the default reading) is what the other reading returns."""
+    from paper_2502_00920_gb300 import inputs as I
+    nx, ny = 7, 5
+    alpha, beta, gamma = 3.0, 0.75, -1.25  # binary fractions: every value below is exact
+    X, Y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)  # node centres, spacing 1
+    a = alpha + beta * X + gamma * Y
+    x = {None: 2, "left": 0, "right": nx - 1}[xwall]
+    y = {None: 3, "bottom": 0, "top": ny - 1}[ywall]
+    # the wall position along each crossed normal; the node's own coordinate otherwise
+    Xw = {None: x + 0.5, "left": 0.0, "right": float(nx)}[xwall]
+    Yw = {None: y + 0.5, "bottom": 0.0, "top": float(ny)}[ywall]
+    at_wall = alpha + beta * Xw + gamma * Yw
+    case = I.Case("w", nx, ny, 0, model="le")
+    lin = oracle_mod.wall_value(case.replace(extrap="linear"), a, x, y, xwall, ywall)
+    own = oracle_mod.wall_value(case.replace(extrap="own"), a, x, y, xwall, ywall)
+    assert lin == at_wall, (lin, at_wall)
+    assert own == a[y, x]
+    # the pin discriminates: other coefficients on the same inner nodes miss it
+    xi = {None: x, "left": x + 1, "right": x - 1}[xwall]
+    yi = {None: y, "bottom": y + 1, "top": y - 1}[ywall]
+    for coef in (0.0, 0.25, 1.0):
+        other = a[y, x] + coef * (a[y, x] - a[y, xi]) + coef * (a[y, x] - a[yi, x])
+        assert other != at_wall
+    # a node that is not on the named wall is refused
+    assert np.isnan(oracle_mod.wall_value(case, a, 2, 2, "left", None))
