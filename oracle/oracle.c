@@ -660,6 +660,30 @@ void ora_step(ora_sim *s, long nsteps) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* the carried state (for the stability analysis of the one-step map)       */
+
+long ora_state_size(const ora_sim *s) { return 21 * s->n; }
+
+/* f [9][n], u [2][n], P [4][n], Pi(H) [4][n], S [2][n], in that order */
+void ora_get_state(const ora_sim *s, double *x) {
+  long n = s->n;
+  memcpy(x, s->f, sizeof(double) * 9 * n);
+  memcpy(x + 9 * n, s->u, sizeof(double) * 2 * n);
+  memcpy(x + 11 * n, s->P, sizeof(double) * 4 * n);
+  memcpy(x + 15 * n, s->Ph, sizeof(double) * 4 * n);
+  memcpy(x + 19 * n, s->S, sizeof(double) * 2 * n);
+}
+
+void ora_set_state(ora_sim *s, const double *x) {
+  long n = s->n;
+  memcpy(s->f, x, sizeof(double) * 9 * n);
+  memcpy(s->u, x + 9 * n, sizeof(double) * 2 * n);
+  memcpy(s->P, x + 11 * n, sizeof(double) * 4 * n);
+  memcpy(s->Ph, x + 15 * n, sizeof(double) * 4 * n);
+  memcpy(s->S, x + 19 * n, sizeof(double) * 2 * n);
+}
+
+/* ------------------------------------------------------------------------ */
 /* outputs                                                                   */
 
 void ora_gradient(const ora_config *cfg, const double *u_aos, double *H_aos) {

@@ -89,6 +89,16 @@ void ora_fields(const ora_sim *s, double *u, double *v, double *P);
 void ora_destroy(ora_sim *s);
 int ora_threads(void);
 
+/* The state one iteration hands to the next, as a flat vector of
+ * ora_state_size(s) doubles: the distributions f (before collision, [9][n]),
+ * u ([2][n]), and P, Pi(H) ([4][n] each) and the source S ([2][n]) as they
+ * stand (functions of u in the text order, of the previous u in the listing
+ * order); node i = y*nx + x.  With the linear material and zero loads one
+ * iteration is a linear map of this vector (used by the stability tests). */
+long ora_state_size(const ora_sim *s);
+void ora_get_state(const ora_sim *s, double *x);
+void ora_set_state(ora_sim *s, const double *x);
+
 /* Building blocks, exported for the pin tests. */
 void ora_first_piola(int model, double lam, double mu, const double H[4], double P[4]);
 void ora_pi_of_h(double mu, const double H[4], double Pi[4]);

@@ -68,6 +68,10 @@ def lib():
         L.ora_fields.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
         L.ora_destroy.argtypes = [ctypes.c_void_p]
         L.ora_threads.restype = ctypes.c_int
+        L.ora_state_size.restype = ctypes.c_long
+        L.ora_state_size.argtypes = [ctypes.c_void_p]
+        L.ora_get_state.argtypes = [ctypes.c_void_p, _dp]
+        L.ora_set_state.argtypes = [ctypes.c_void_p, _dp]
         L.ora_params.argtypes = [ctypes.POINTER(_Config), _dp]
         L.ora_first_piola.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp]
         L.ora_pi_of_h.argtypes = [ctypes.c_double, _dp, _dp]
@@ -153,6 +157,17 @@ class OracleSim:
         P = np.empty((ny, nx, 4))
         lib().ora_fields(self._h, _ptr(u), _ptr(v), _ptr(P))
         return u, v, P
+
+    def state(self) -> np.ndarray:
+        """The carried state (f, u, P, Pi(H), S) as one float64 vector."""
+        x = np.empty(int(lib().ora_state_size(self._h)))
+        lib().ora_get_state(self._h, _ptr(x))
+        return x
+
+    def set_state(self, x) -> None:
+        x = _f64(x)
+        assert x.size == int(lib().ora_state_size(self._h))
+        lib().ora_set_state(self._h, _ptr(x))
 
     def close(self) -> None:
         if getattr(self, "_h", None):
