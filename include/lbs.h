@@ -196,7 +196,10 @@ int lbs_fields_device(lbs_handle *h, double *u, double *v, double *P);
  *    three); larger rows are rejected with LBS_EINVAL.
  *  - The first call on a device (with that device current, as for every
  *    call on the handle) looks up the array's device address; make that
- *    first call before any stream capture.
+ *    first call before any stream capture.  After a device reset the next
+ *    call looks it up again (the address belongs to the destroyed context).
+ *  - On an error the call still waits for the copies it queued before
+ *    returning, so no host buffer is written after it returns.
  *  - Every call on a device shares the one array, which keeps the last
  *    call's contents; each call overwrites every entry it copies out, so
  *    nothing needs clearing.  Calls that overlapped on the GPU would race on

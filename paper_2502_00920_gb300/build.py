@@ -16,8 +16,11 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liblbs.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-Xcompiler", "-Wall"]
+# --fmad=false: no implicit contraction of products and sums into fused
+# multiply-adds; the kernels write the fused ones they want (fmr), so a node's
+# rounding is fixed by the source in every kernel that computes it
+FLAGS = ["-O3", "--fmad=false", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+         "-Xcompiler", "-Wall", "-Xcompiler", "-ffp-contract=off"]
 UNITS = ["lbs_api.cu", "lbs_autotune.cu", "lbs_serve.cu", "lbs_fields_static.cu", "lbs_selftest.cu", "kernels_fp64.cu",
          "kernels_fp32.cu", "kernels_fp16.cu"]
 

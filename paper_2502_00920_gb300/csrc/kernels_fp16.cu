@@ -65,6 +65,8 @@ int kernels_per_step(const Params &p, int v) {
   }
 }
 
+int iterations_per_call(const Params &, int) { return 1; }
+
 bool tma_maps(const Params &p, int v, const void *g, const void *u, void *og, void *ou) {
   if (v == 6) return make_march_maps<V4, M6>(p, g, u, og, ou);
   if (v == 7) return make_tma_maps<V3>(p, g, u, og, ou);
@@ -74,11 +76,14 @@ bool tma_maps(const Params &p, int v, const void *g, const void *u, void *og, vo
 
 const Launchers kL = {kVariants,
                       (1 << 4) | (1 << 5) | (1 << 6) | (1 << 7),
-                      5,  // default: the fastest on the 16384^2 roofline lattice
+                      7,  // default: the fastest on the 16384^2 roofline lattice
                       shape,
                       name,
                       step,
                       kernels_per_step,
+                      iterations_per_call,
+                      launch_step<V0>,
+                      step_kernel_count<V0>,
                       tma_maps,
                       launch_init<V0>,
                       launch_fields<V0>,

@@ -11,14 +11,14 @@ using V2 = Cfg<P, 64, 8, 4>;
 using V3 = Cfg<P, 32, 24, 8>;
 using V4 = Cfg<P, 32, 16, 8>;
 using M6 = MarchCfg<V4, 8, 128, 2>;
+using V8 = Cfg<P, 32, 32, 8>;
+using V9 = Cfg<P, 32, 16, 16>;  // one node per thread, 512 threads
 // 0-3: V0-V3 tiles read from global memory; 4: V4 tiles staged by TMA;
 // 5: V4 tiles, persistent blocks with a two-stage TMA ring; 6: row-marching
-// strips over the V4 tile columns; 7: V3 tiles staged by TMA.
-// FP32 tiles with four or more nodes per thread (TY / thread rows >= 4) are
-// not compiled: their frame kernel gave wrong values at wall nodes.
-constexpr int kVariants = 8;
-static_assert(V0::CPT <= 3 && V1::CPT <= 3 && V2::CPT <= 3 && V3::CPT <= 3 && V4::CPT <= 3,
-              "FP32 tiles take at most three nodes per thread");
+// strips over the V4 tile columns; 7: V3 tiles staged by TMA; 8: V8 tiles
+// (four nodes per thread) read from global memory; 9: two fused iterations per
+// launch on V9 tiles (periodic lattices; one V0 iteration per call otherwise).
+constexpr int kVariants = 10;
 
 TileShape shape(int v) {
   switch (v) {
@@ -29,6 +29,8 @@ TileShape shape(int v) {
     case 4:
     case 5:
     case 6: return {V4::TX, V4::TY};
+    case 8: return {V8::TX, V8::TY};
+    case 9: return {V9::TX, V9::TY};
     default: return {V0::TX, V0::TY};
   }
 }
@@ -39,6 +41,7 @@ const char *name(int v) {
     case 5: return "step_tma2_kernel";
     case 6: return "step_march_kernel";
     case 7: return "step_tma_kernel";
+    case 9: return "step_fused2_tma_kernel";
     default: return "step_interior_kernel";
   }
 }
@@ -52,6 +55,8 @@ cudaError_t step(const Params &p, const StepPtrs &s, int v, cudaStream_t st) {
     case 5: return launch_step_tma2<V4>(p, s, st);
     case 6: return launch_step_march<V4, M6>(p, s, st);
     case 7: return launch_step_tma<V3>(p, s, st);
+    case 8: return launch_step<V8>(p, s, st);
+    case 9: return fused2_applies(p) ? launch_step_fused2<V9>(p, s, st) : launch_step<V0>(p, s, st);
     default: return launch_step<V0>(p, s, st);
   }
 }
@@ -65,11 +70,23 @@ int kernels_per_step(const Params &p, int v) {
     case 4:
     case 5:
     case 6: return step_kernel_count<V4>(p);
+    case 8: return step_kernel_count<V8>(p);
+    case 9: {
+      if (!fused2_applies(p)) return step_kernel_count<V0>(p);
+      const int ntx = (p.nx + V9::TX - 1) / V9::TX, nty = (p.ny + V9::TY - 1) / V9::TY;
+      int a_lo, a_hi, b_lo, b_hi;
+      interior_range_m(p.nx, p.ny, V9::TX, V9::TY, 6, a_lo, a_hi, b_lo, b_hi);
+      const int ni = (a_hi - a_lo) * (b_hi - b_lo);
+      return (ni > 0 ? 1 : 0) + (ntx * nty > ni ? 1 : 0);
+    }
     default: return step_kernel_count<V0>(p);
   }
 }
 
+int iterations_per_call(const Params &p, int v) { return v == 9 && fused2_applies(p) ? 2 : 1; }
+
 bool tma_maps(const Params &p, int v, const void *g, const void *u, void *og, void *ou) {
+  if (v == 9) return make_fused2_maps<V9>(p, g, u, og, ou);
   if (v == 6) return make_march_maps<V4, M6>(p, g, u, og, ou);
   if (v == 7) return make_tma_maps<V3>(p, g, u, og, ou);
   if (v != 4 && v != 5) return false;
@@ -77,12 +94,15 @@ bool tma_maps(const Params &p, int v, const void *g, const void *u, void *og, vo
 }
 
 const Launchers kL = {kVariants,
-                      (1 << 4) | (1 << 5) | (1 << 6) | (1 << 7),
+                      (1 << 4) | (1 << 5) | (1 << 6) | (1 << 7) | (1 << 9),
                       4,  // default: the fastest on the 16384^2 roofline lattice
                       shape,
                       name,
                       step,
                       kernels_per_step,
+                      iterations_per_call,
+                      launch_step<V0>,
+                      step_kernel_count<V0>,
                       tma_maps,
                       launch_init<V0>,
                       launch_fields<V0>,

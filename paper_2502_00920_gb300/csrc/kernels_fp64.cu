@@ -49,6 +49,8 @@ int kernels_per_step(const Params &p, int v) {
   }
 }
 
+int iterations_per_call(const Params &, int) { return 1; }
+
 bool tma_maps(const Params &p, int v, const void *g, const void *u, void *og, void *ou) {
   if (v != 4) return false;
   return make_tma_maps<V4>(p, g, u, og, ou);
@@ -61,6 +63,9 @@ const Launchers kL = {kVariants,
                       name,
                       step,
                       kernels_per_step,
+                      iterations_per_call,
+                      launch_step<V0>,
+                      step_kernel_count<V0>,
                       tma_maps,
                       launch_init<V0>,
                       launch_fields<V0>,

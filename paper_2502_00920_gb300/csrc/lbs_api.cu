@@ -265,8 +265,10 @@ int capture_graph(lbs_handle *h, int parity) {
   cudaGraph_t graph = nullptr;
   LBS_CK(cudaStreamBeginCapture(h->own_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
-  for (int i = 0; i < h->graph_chunk && err == cudaSuccess; ++i)
-    err = h->L->step(h->P, ptrs(h, parity ^ (i & 1), h->kdev, i), h->variant, h->own_stream);
+  // graph_chunk iterations: calls of iterations_per_call iterations each
+  const int its = h->L->iterations_per_call(h->P, h->variant);
+  for (int i = 0; i < h->graph_chunk / its && err == cudaSuccess; ++i)
+    err = h->L->step(h->P, ptrs(h, parity ^ (i & 1), h->kdev, (int64_t)i * its), h->variant, h->own_stream);
   if (err == cudaSuccess) {
     add_counter_kernel<<<1, 1, 0, h->own_stream>>>(h->kdev, h->graph_chunk);
     err = cudaGetLastError();
@@ -602,16 +604,29 @@ int lbs_step(lbs_handle *h, int64_t n) {
         h->launches += 1;
       }
       LBS_CK(cudaGraphLaunch(h->graph[h->parity], h->stream));
-      h->launches += (int64_t)h->graph_chunk * h->L->kernels_per_step(h->P, h->variant) + 1;
+      const int its = h->L->iterations_per_call(h->P, h->variant), calls = h->graph_chunk / its;
+      h->launches += (int64_t)calls * h->L->kernels_per_step(h->P, h->variant) + 1;
+      h->parity ^= calls & 1;  // the buffers swap once per call
       h->k += h->graph_chunk;
       h->kdev_value = h->k;
       n -= h->graph_chunk;
     } else {
-      LBS_CK(h->L->step(h->P, ptrs(h, h->parity, h->zero_dev, h->k), h->variant, h->stream));
-      h->launches += h->L->kernels_per_step(h->P, h->variant);
+      const int its = h->L->iterations_per_call(h->P, h->variant);
+      if (its > 1 && n >= its) {
+        LBS_CK(h->L->step(h->P, ptrs(h, h->parity, h->zero_dev, h->k), h->variant, h->stream));
+        h->launches += h->L->kernels_per_step(h->P, h->variant);
+      } else if (its > 1) {
+        // the last iteration of an odd count under a fused variant
+        LBS_CK(h->L->step1(h->P, ptrs(h, h->parity, h->zero_dev, h->k), h->stream));
+        h->launches += h->L->kernels_per_step1(h->P);
+      } else {
+        LBS_CK(h->L->step(h->P, ptrs(h, h->parity, h->zero_dev, h->k), h->variant, h->stream));
+        h->launches += h->L->kernels_per_step(h->P, h->variant);
+      }
+      const int done = (its > 1 && n >= its) ? its : 1;
       h->parity ^= 1;
-      h->k += 1;
-      n -= 1;
+      h->k += done;
+      n -= done;
     }
     // monitors run at the first chunk boundary at or after each multiple of the interval
     if (h->mon_interval > 0 && h->k >= h->next_mon) {

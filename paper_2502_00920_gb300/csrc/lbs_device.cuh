@@ -31,10 +31,7 @@
 namespace lbs {
 
 // ------------------------------------------------------------------ D2Q9
-// Tab. 1: c_q = c (ex(q), ey(q)); weights 4/9, 1/9 (axes), 1/36 (diagonals)
-__host__ __device__ constexpr int ex(int q) { return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0); }
-__host__ __device__ constexpr int ey(int q) { return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0); }
-__host__ __device__ constexpr int opp(int q) { return q == 0 ? 0 : (q <= 4 ? ((q + 1) % 4) + 1 : ((q - 3) % 4) + 5); }
+// Tab. 1: c_q = c (ex(q), ey(q)) (lbs_tiles.h); weights 4/9, 1/9 (axes), 1/36 (diagonals)
 template <class R>
 __host__ __device__ constexpr R wq(int q) { return q == 0 ? R(4) / R(9) : (q <= 4 ? R(1) / R(9) : R(1) / R(36)); }
 
@@ -123,6 +120,27 @@ __device__ __forceinline__ void u_make(double x, double y, float4 &out) {
   out = make_float4(hx, hy, (float)(x - (double)hx), (float)(y - (double)hy));
 }
 
+// a * b + c with a single rounding.  The library is compiled without
+// implicit contraction (nvcc --fmad=false): every product and sum not written
+// with fmr rounds on its own, so the rounding of each expression is fixed by
+// the source, and every tile shape, frame and batch kernel computes a node
+// with the same operations whatever the compiler inlines or schedules.
+__host__ __device__ __forceinline__ float fmr(float a, float b, float c) { return fmaf(a, b, c); }
+__host__ __device__ __forceinline__ double fmr(double a, double b, double c) { return fma(a, b, c); }
+
+// First moment sum_q e_q v_q of nine populations (index 0 unused), from the
+// differences of opposite pairs.  In a near-static state each population is
+// close to its opposite, so every pair difference is exact (Sterbenz) and the
+// sum rounds relative to the momentum, not to the populations it is a small
+// difference of: in single precision the displacement increment then keeps
+// its relative accuracy over long, slow loadings.
+template <class R>
+__host__ __device__ __forceinline__ void first_moment(const R v[9], R &mx, R &my) {
+  const R d57 = v[5] - v[7], d68 = v[6] - v[8];
+  mx = (v[1] - v[3]) + (d57 - d68);
+  my = (v[2] - v[4]) + (d57 + d68);
+}
+
 // ------------------------------------------------------------------ material
 // N(H) = P(H) + Pi(H), Pi(H) = -mu (H + H^T + tr H I), written so that no
 // term cancels at small strain (Sect. 4 laws, rearranged):
@@ -143,29 +161,31 @@ __host__ __device__ inline void constitutive_n(int model, R lam, R mu, const R H
     N[3] = d;
   } else if (model == LBS_SVK) {
     // H^T H
-    const R c11 = h11 * h11 + h21 * h21, c12 = h11 * h12 + h21 * h22, c22 = h12 * h12 + h22 * h22;
-    const R trE = trH + R(0.5) * (c11 + c22);
-    const R s11 = lam * trE + mu * (R(2) * h11 + c11);
-    const R s12 = mu * (h12 + h21 + c12);
-    const R s22 = lam * trE + mu * (R(2) * h22 + c22);
-    const R d = lam * trE - mu * trH;
-    N[0] = d + mu * c11 + h11 * s11 + h12 * s12;
-    N[1] = mu * c12 + h11 * s12 + h12 * s22;
-    N[2] = mu * c12 + h21 * s11 + h22 * s12;
-    N[3] = d + mu * c22 + h21 * s12 + h22 * s22;
+    const R c11 = fmr(h11, h11, h21 * h21), c12 = fmr(h11, h12, h21 * h22), c22 = fmr(h12, h12, h22 * h22);
+    const R trE = fmr(R(0.5), c11 + c22, trH);
+    const R s11 = fmr(lam, trE, mu * (R(2) * h11 + c11));
+    const R s12 = mu * ((h12 + h21) + c12);
+    const R s22 = fmr(lam, trE, mu * (R(2) * h22 + c22));
+    const R d = fmr(lam, trE, -(mu * trH));
+    const R mc12 = mu * c12;
+    N[0] = fmr(h12, s12, fmr(h11, s11, fmr(mu, c11, d)));
+    N[1] = fmr(h12, s22, fmr(h11, s12, mc12));
+    N[2] = fmr(h22, s12, fmr(h21, s11, mc12));
+    N[3] = fmr(h22, s22, fmr(h21, s12, fmr(mu, c22, d)));
   } else {  // LBS_NH
-    const R detH = h11 * h22 - h12 * h21;
+    const R detH = fmr(h11, h22, -(h12 * h21));
     const R a = trH + detH;
     const R J = R(1) + a;
     const R iJ = R(1) / J;
     const R m = mu * iJ;
     const R l = R(0.5) * lam * a * (a + R(2)) * iJ;
-    const R diag = m * (a - (R(2) + a) * trH);
+    const R diag = m * fmr(-(R(2) + a), trH, a);
+    const R ma = m * a;
     // I + K = [[1 + h22, -h21], [-h12, 1 + h11]]
-    N[0] = -m * a * h11 + diag + l * (R(1) + h22);
-    N[1] = -m * a * h21 - l * h21;
-    N[2] = -m * a * h12 - l * h12;
-    N[3] = -m * a * h22 + diag + l * (R(1) + h11);
+    N[0] = fmr(-ma, h11, fmr(l, R(1) + h22, diag));
+    N[1] = -((ma + l) * h21);
+    N[2] = -((ma + l) * h12);
+    N[3] = fmr(-ma, h22, fmr(l, R(1) + h11, diag));
   }
 }
 
@@ -174,7 +194,7 @@ __host__ __device__ inline void constitutive_n(int model, R lam, R mu, const R H
 template <class R>
 __device__ __forceinline__ void material(const Params &P, R lam, R mu, const R H[4], R N[4]) {
   if (sizeof(R) == 4 && P.model == LBS_NH) {
-    const R J = R(1) + (H[0] + H[3]) + (H[0] * H[3] - H[1] * H[2]);
+    const R J = R(1) + ((H[0] + H[3]) + fmr(H[0], H[3], -(H[1] * H[2])));
     if (J < R(0.5)) {
       double Hd[4] = {H[0], H[1], H[2], H[3]}, Nd[4];
       constitutive_n<double>(P.model, P.lam, P.mu, Hd, Nd);
@@ -234,9 +254,8 @@ __device__ inline void edge_value(const Params &P, int e, int64_t k, double out[
 template <class R, class G, bool LIN>
 __device__ void wall_rules(const Params &P, const R *bnd, const G *g, const double (*sev)[2], int x, int y,
                            const R g0[9], unsigned mask, R f[9], R gsc) {
-  int xw = -1, yw = -1;
-  if (!P.per_x) xw = (x == 0) ? kLeft : ((x == P.nx - 1) ? kRight : -1);
-  if (!P.per_y) yw = (y == 0) ? kBottom : ((y == P.ny - 1) ? kTop : -1);
+  int xw, yw;
+  walls_of(P, x, y, xw, yw);
   const bool xn = xw >= 0 && P.etype[xw] == LBS_NEUMANN;
   const bool yn = yw >= 0 && P.etype[yw] == LBS_NEUMANN;
   // Pi*/cs^2 from N and T* is brought into the units of g (times gsc)
@@ -255,14 +274,14 @@ __device__ void wall_rules(const Params &P, const R *bnd, const G *g, const doub
   const R Axx_o = R(3) * mxx, Axy_o = R(3) * mxy, Ayy_o = R(3) * myy;
   R Axx_x = 0, axy_x = 0, Ayy_y = 0, axy_y = 0;
   if (xn) {
-    const R *Nn = bnd + ((size_t)xw * P.blen + y) * 4;  // N11, N12, N21, N22
+    const R *Nn = bnd + side_entry(P, 0, xw, y);  // N11, N12, N21, N22
     const double *T = sev[xw];
     const R s = (xw == kRight) ? R(1) : R(-1);
     Axx_x = (Nn[0] - s * (R)T[0]) * ics2;
     axy_x = (Nn[2] - s * (R)T[1]) * ics2;
   }
   if (yn) {
-    const R *Nn = bnd + ((size_t)yw * P.blen + x) * 4;
+    const R *Nn = bnd + side_entry(P, 0, yw, x);
     const double *T = sev[yw];
     const R s = (yw == kTop) ? R(1) : R(-1);
     Ayy_y = (Nn[3] - s * (R)T[1]) * ics2;
@@ -274,14 +293,13 @@ __device__ void wall_rules(const Params &P, const R *bnd, const G *g, const doub
   R dX[4] = {0, 0, 0, 0}, dY[4] = {0, 0, 0, 0}, nX[4] = {0, 0, 0, 0}, nY[4] = {0, 0, 0, 0};
   if (LIN && P.extrap) {
     const size_t plane = (size_t)P.ny * P.pitch;
-    const R *inner = bnd + (size_t)4 * P.blen * 4;  // second layer of the side array
     const R own[4] = {r, Axx_o, Axy_o, Ayy_o};
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
       const int e = w == 0 ? xw : yw;
       if (e < 0) continue;
-      const int xi = w == 0 ? (e == kLeft ? x + 1 : x - 1) : x;
-      const int yi = w == 0 ? y : (e == kBottom ? y + 1 : y - 1);
+      int xi, yi;
+      inner_node(e, x, y, xi, yi);
       const size_t idx = (size_t)yi * P.pitch + xi;
       R ri = 0, ixx = 0, ixy = 0, iyy = 0;
 #pragma unroll
@@ -294,8 +312,8 @@ __device__ void wall_rules(const Params &P, const R *bnd, const G *g, const doub
       }
       const R in[4] = {ri, R(3) * ixx, R(3) * ixy, R(3) * iyy};
       const int pos = w == 0 ? y : x;
-      const R *N0 = bnd + ((size_t)e * P.blen + pos) * 4;
-      const R *N1 = inner + ((size_t)e * P.blen + pos) * 4;
+      const R *N0 = bnd + side_entry(P, 0, e, pos);
+      const R *N1 = bnd + side_entry(P, 1, e, pos);
       R *d = w == 0 ? dX : dY;
       R *n = w == 0 ? nX : nY;
 #pragma unroll
@@ -309,8 +327,8 @@ __device__ void wall_rules(const Params &P, const R *bnd, const G *g, const doub
 #pragma unroll
   for (int q = 1; q < 9; ++q) {
     if (!(mask & (1u << q))) continue;
-    const bool ox = !P.per_x && ((ex(q) == 1 && x == 0) || (ex(q) == -1 && x == P.nx - 1));
-    const bool oy = !P.per_y && ((ey(q) == 1 && y == 0) || (ey(q) == -1 && y == P.ny - 1));
+    bool ox, oy;
+    link_crosses(P, x, y, q, ox, oy);
     const bool dxw = ox && P.etype[xw] == LBS_DIRICHLET;
     const bool dyw = oy && P.etype[yw] == LBS_DIRICHLET;
     const int qb = opp(q);
@@ -373,77 +391,45 @@ template <class R>
 __device__ __forceinline__ void collide(R f[9], R Sx, R Sy, R omega, R sigma) {
   const R s13 = f[1] + f[3], s24 = f[2] + f[4], s57 = f[5] + f[7], s68 = f[6] + f[8];
   const R d13 = f[1] - f[3], d24 = f[2] - f[4], d57 = f[5] - f[7], d68 = f[6] - f[8];
-  const R Q = f[0] - R(2) * (s13 + s24) + R(4) * (s57 + s68);
+  // (the products by 2 and 4 are exact)
+  const R Q = fmr(R(4), s57 + s68, fmr(R(-2), s13 + s24, f[0]));
   const R c3 = R(1) / R(3), c6 = R(1) / R(6), c12 = R(1) / R(12);
-  const R ox = d13 * c6 - (d57 - d68) * c3;
-  const R oy = d24 * c6 - (d57 + d68) * c3;
-  const R o57 = d57 * c3 - (d13 + d24) * c12;
-  const R o68 = d68 * c3 - (d24 - d13) * c12;
+  const R ox = fmr(d13, c6, -((d57 - d68) * c3));
+  const R oy = fmr(d24, c6, -((d57 + d68) * c3));
+  const R o57 = fmr(d57, c3, -((d13 + d24) * c12));
+  const R o68 = fmr(d68, c3, -((d24 - d13) * c12));
   const R ne0 = Q * (R(1) / R(9)), ne1 = Q * (R(-1) / R(18)), ne5 = Q * (R(1) / R(36));
-  const R fx = sigma * Sx * (R(1) / R(9)), fy = sigma * Sy * (R(1) / R(9));
-  const R f57 = sigma * (Sx + Sy) * (R(1) / R(36)), f68 = sigma * (Sy - Sx) * (R(1) / R(36));
-  f[0] = f[0] - omega * ne0;
-  f[1] = f[1] - omega * (ne1 + ox) + fx;
-  f[3] = f[3] - omega * (ne1 - ox) - fx;
-  f[2] = f[2] - omega * (ne1 + oy) + fy;
-  f[4] = f[4] - omega * (ne1 - oy) - fy;
-  f[5] = f[5] - omega * (ne5 + o57) + f57;
-  f[7] = f[7] - omega * (ne5 - o57) - f57;
-  f[6] = f[6] - omega * (ne5 + o68) + f68;
-  f[8] = f[8] - omega * (ne5 - o68) - f68;
+  const R sx = sigma * Sx, sy = sigma * Sy;
+  const R fx = sx * (R(1) / R(9)), fy = sy * (R(1) / R(9));
+  const R f57 = (sx + sy) * (R(1) / R(36)), f68 = (sy - sx) * (R(1) / R(36));
+  const R mo = -omega;
+  f[0] = fmr(mo, ne0, f[0]);
+  f[1] = fmr(mo, ne1 + ox, f[1]) + fx;
+  f[3] = fmr(mo, ne1 - ox, f[3]) - fx;
+  f[2] = fmr(mo, ne1 + oy, f[2]) + fy;
+  f[4] = fmr(mo, ne1 - oy, f[4]) - fy;
+  f[5] = fmr(mo, ne5 + o57, f[5]) + f57;
+  f[7] = fmr(mo, ne5 - o57, f[7]) - f57;
+  f[6] = fmr(mo, ne5 + o68, f[6]) + f68;
+  f[8] = fmr(mo, ne5 - o68, f[8]) - f68;
 }
 
 // ------------------------------------------------------------------ tiles
 // A thread block owns a TX x TY tile of nodes; NTY thread rows, each thread
 // handles CPT = TY / NTY nodes of one column.  Shared memory holds u_{k+1}
 // on the tile plus a 2-node halo (R2) and N on the tile plus a 1-node halo (R1).
+// (geometry and index arithmetic in lbs_tiles.h: TileGeom, ring_pos, locate)
 template <class Pr, int TX_, int TY_, int NTY_>
-struct TileCfg {
+struct TileCfg : TileGeom<TX_, TY_, NTY_> {
+  using G = TileGeom<TX_, TY_, NTY_>;
   using real = typename Pr::real;
   using us = typename Pr::us;
   using gs = typename Pr::gs;
-  static constexpr int TX = TX_, TY = TY_, NTY = NTY_;
-  static constexpr int NT = TX * NTY, CPT = TY / NTY;
-  static constexpr int R2W = TX + 4, R2H = TY + 4, R1W = TX + 2, R1H = TY + 2;
-  static constexpr int NRING = R2W * R2H - TX * TY;
   struct Smem {
-    us u[R2H][R2W];
-    real n[4][R1H][R1W];
+    us u[G::R2H][G::R2W];
+    real n[4][G::R1H][G::R1W];
   };
-  static_assert(TY % NTY == 0, "tile rows must split evenly over thread rows");
 };
-
-// position of ring entry r of R2 (the 2-node frame around the tile)
-template <class C>
-__device__ __forceinline__ void ring_pos(int r, int &rx, int &ry) {
-  constexpr int top = 2 * C::R2W;
-  if (r < top) {
-    ry = r / C::R2W;
-    rx = r % C::R2W;
-  } else if (r < 2 * top) {
-    r -= top;
-    ry = C::TY + 2 + r / C::R2W;
-    rx = r % C::R2W;
-  } else {
-    r -= 2 * top;
-    ry = 2 + r / 4;
-    const int c = r % 4;
-    rx = c < 2 ? c : C::TX + c;
-  }
-}
-
-// wrap (periodic) or reject a node coordinate; returns false outside
-__device__ __forceinline__ bool locate(const Params &P, int &x, int &y) {
-  if (x < 0 || x >= P.nx) {
-    if (!P.per_x) return false;
-    x = (x + P.nx) % P.nx;
-  }
-  if (y < 0 || y >= P.ny) {
-    if (!P.per_y) return false;
-    y = (y + P.ny) % P.ny;
-  }
-  return true;
-}
 
 // Stream into node (x, y) (already wrapped into the lattice) and return the
 // first moments sum_q e_q g_q (own node, post-collision at k) and
@@ -471,17 +457,8 @@ __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *_
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       g0[q] = gload(g, q * plane + idx, inv);
-      int sx = x - ex(q), sy = y - ey(q);
-      bool out = false;
-      if (sx < 0 || sx >= P.nx) {
-        if (P.per_x) sx = (sx + P.nx) % P.nx;
-        else out = true;
-      }
-      if (sy < 0 || sy >= P.ny) {
-        if (P.per_y) sy = (sy + P.ny) % P.ny;
-        else out = true;
-      }
-      if (out) {
+      int sx, sy;
+      if (!stream_source(P, x, y, q, sx, sy)) {
         mask |= 1u << q;
         f[q] = 0;
       } else {
@@ -497,18 +474,10 @@ __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *_
     size_t src[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-      int sx = x - ex(q), sy = y - ey(q);
-      bool out = false;
-      if (sx < 0 || sx >= P.nx) {
-        if (P.per_x) sx = sx < 0 ? sx + P.nx : sx - P.nx;
-        else out = true;
-      }
-      if (sy < 0 || sy >= P.ny) {
-        if (P.per_y) sy = sy < 0 ? sy + P.ny : sy - P.ny;
-        else out = true;
-      }
-      if (out) mask |= 1u << q;
-      src[q] = out ? idx : (size_t)sy * P.pitch + sx;
+      int sx, sy;
+      const bool in = stream_source(P, x, y, q, sx, sy);
+      if (!in) mask |= 1u << q;
+      src[q] = in ? (size_t)sy * P.pitch + sx : idx;
     }
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -520,23 +489,20 @@ __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *_
       if (mask & (1u << q)) f[q] = 0;
     if (mask) wall_rules<R, typename Pr::gs, LIN>(P, bnd, g, sev, x, y, g0, mask, f, gsc);
   }
-  gx = (g0[1] - g0[3]) + (g0[5] - g0[6]) + (g0[8] - g0[7]);
-  gy = (g0[2] - g0[4]) + (g0[5] - g0[8]) + (g0[6] - g0[7]);
-}
-
-__device__ __forceinline__ bool on_wall(const Params &P, int x, int y) {
-  return (!P.per_x && (x == 0 || x == P.nx - 1)) || (!P.per_y && (y == 0 || y == P.ny - 1));
+  first_moment(g0, gx, gy);
 }
 
 // store N of wall node (x, y) into the side array entries of its walls
 template <class R>
 __device__ __forceinline__ void store_wall_n(const Params &P, R *bnd, int x, int y, const R N[4]) {
-  if (!P.per_x && (x == 0 || x == P.nx - 1)) {
-    R *d = bnd + ((size_t)(x == 0 ? kLeft : kRight) * P.blen + y) * 4;
+  int xw, yw;
+  walls_of(P, x, y, xw, yw);
+  if (xw >= 0) {
+    R *d = bnd + side_entry(P, 0, xw, y);
     for (int m = 0; m < 4; ++m) d[m] = N[m];
   }
-  if (!P.per_y && (y == 0 || y == P.ny - 1)) {
-    R *d = bnd + ((size_t)(y == 0 ? kBottom : kTop) * P.blen + x) * 4;
+  if (yw >= 0) {
+    R *d = bnd + side_entry(P, 0, yw, x);
     for (int m = 0; m < 4; ++m) d[m] = N[m];
   }
 }
@@ -545,18 +511,11 @@ __device__ __forceinline__ void store_wall_n(const Params &P, R *bnd, int x, int
 // second layer for each wall it lies one step inwards from
 template <class R>
 __device__ __forceinline__ void store_inner_n(const Params &P, R *bnd, int x, int y, const R N[4]) {
-  R *inner = bnd + (size_t)4 * P.blen * 4;
-  auto put = [&](int e, int pos) {
-    R *d = inner + ((size_t)e * P.blen + pos) * 4;
+  int e[4], pos[4];
+  const int n = inner_entries(P, x, y, e, pos);
+  for (int i = 0; i < n; ++i) {
+    R *d = bnd + side_entry(P, 1, e[i], pos[i]);
     for (int m = 0; m < 4; ++m) d[m] = N[m];
-  };
-  if (!P.per_x) {
-    if (x == 1) put(kLeft, y);
-    if (x == P.nx - 2) put(kRight, y);
-  }
-  if (!P.per_y) {
-    if (y == 1) put(kBottom, x);
-    if (y == P.ny - 2) put(kTop, x);
   }
 }
 
@@ -571,18 +530,10 @@ struct Fd {
                                               int gyn, R idx_, R H[4]) {
     R dxx, dxy, dyx, dyy;  // d u_x/dx, d u_y/dx, d u_x/dy, d u_y/dy
     const int cx = rx + 1, cy = ry + 1;
-    R sx = R(0.5) * idx_, sy = R(0.5) * idx_;
-    int xa = cx + 1, xb = cx - 1, ya = cy + 1, yb = cy - 1;
-    if (EDGE) {
-      if (!P.per_x) {
-        if (gxn == 0) { xb = cx; sx = idx_; }
-        else if (gxn == P.nx - 1) { xa = cx; sx = idx_; }
-      }
-      if (!P.per_y) {
-        if (gyn == 0) { yb = cy; sy = idx_; }
-        else if (gyn == P.ny - 1) { ya = cy; sy = idx_; }
-      }
-    }
+    int xa, xb, ya, yb;
+    bool onex, oney;
+    fd_taps<EDGE>(P, cx, cy, gxn, gyn, xa, xb, ya, yb, onex, oney);
+    const R sx = onex ? idx_ : R(0.5) * idx_, sy = oney ? idx_ : R(0.5) * idx_;
     udiff(sm.u[cy][xa], sm.u[cy][xb], dxx, dxy);
     udiff(sm.u[ya][cx], sm.u[yb][cx], dyx, dyy);
     H[0] = dxx * sx;
@@ -593,20 +544,12 @@ struct Fd {
   // S = div N at R1 position (rx, ry) of a tile node
   static __device__ __forceinline__ void div(const typename C::Smem &sm, const Params &P, int rx, int ry, int gxn,
                                              int gyn, R idx_, R &Sx, R &Sy) {
-    R sx = R(0.5) * idx_, sy = R(0.5) * idx_;
-    int xa = rx + 1, xb = rx - 1, ya = ry + 1, yb = ry - 1;
-    if (EDGE) {
-      if (!P.per_x) {
-        if (gxn == 0) { xb = rx; sx = idx_; }
-        else if (gxn == P.nx - 1) { xa = rx; sx = idx_; }
-      }
-      if (!P.per_y) {
-        if (gyn == 0) { yb = ry; sy = idx_; }
-        else if (gyn == P.ny - 1) { ya = ry; sy = idx_; }
-      }
-    }
-    Sx = (sm.n[0][ry][xa] - sm.n[0][ry][xb]) * sx + (sm.n[1][ya][rx] - sm.n[1][yb][rx]) * sy;
-    Sy = (sm.n[2][ry][xa] - sm.n[2][ry][xb]) * sx + (sm.n[3][ya][rx] - sm.n[3][yb][rx]) * sy;
+    int xa, xb, ya, yb;
+    bool onex, oney;
+    fd_taps<EDGE>(P, rx, ry, gxn, gyn, xa, xb, ya, yb, onex, oney);
+    const R sx = onex ? idx_ : R(0.5) * idx_, sy = oney ? idx_ : R(0.5) * idx_;
+    Sx = fmr(sm.n[0][ry][xa] - sm.n[0][ry][xb], sx, (sm.n[1][ya][rx] - sm.n[1][yb][rx]) * sy);
+    Sy = fmr(sm.n[2][ry][xa] - sm.n[2][ry][xb], sx, (sm.n[3][ya][rx] - sm.n[3][yb][rx]) * sy);
   }
 };
 
@@ -626,8 +569,7 @@ __device__ __forceinline__ void phase_n(typename C::Smem &sm, const Params &P, i
     material<R>(P, lam, mu, H, N);
 #pragma unroll
     for (int m = 0; m < 4; ++m) sm.n[m][ry][rx] = N[m];
-    if (EDGE && bnd_out && rx >= 1 && rx <= C::TX && ry >= 1 && ry <= C::TY && x0 - 1 + rx < P.nx &&
-        y0 - 1 + ry < P.ny) {
+    if (EDGE && bnd_out && r1_own_node<C>(P, x0, y0, rx, ry)) {
       if (on_wall(P, gx, gy)) store_wall_n<R>(P, bnd_out, gx, gy, N);
       if (LIN && P.extrap) store_inner_n<R>(P, bnd_out, gx, gy, N);
     }
@@ -672,8 +614,8 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     if (EDGE && !locate(P, x, y)) continue;
     R gxm, gym;
     gather<typename C::PrT, EDGE, LIN>(P, g, bnd, sev, x, y, inv, f[i], gxm, gym, scl);
-    const R fx = (f[i][1] - f[i][3]) + (f[i][5] - f[i][6]) + (f[i][8] - f[i][7]);
-    const R fy = (f[i][2] - f[i][4]) + (f[i][5] - f[i][8]) + (f[i][6] - f[i][7]);
+    R fx, fy;
+    first_moment(f[i], fx, fy);
     sm.u[ly + 2][lx + 2] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
   }
   // phase 1b: the 2-node frame (u only)
@@ -684,8 +626,8 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     if (EDGE && !locate(P, x, y)) continue;
     R ff[9], gxm, gym;
     gather<typename C::PrT, EDGE, LIN>(P, g, bnd, sev, x, y, inv, ff, gxm, gym, scl);
-    const R fx = (ff[1] - ff[3]) + (ff[5] - ff[6]) + (ff[8] - ff[7]);
-    const R fy = (ff[2] - ff[4]) + (ff[5] - ff[8]) + (ff[6] - ff[7]);
+    R fx, fy;
+    first_moment(ff, fx, fy);
     sm.u[ry][rx] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
   }
   __syncthreads();
@@ -723,27 +665,8 @@ __global__ void __launch_bounds__(C::NT) step_interior_kernel(const Params P, co
   step_tile<C, false>(P, S, (a_lo + blockIdx.x) * C::TX, (b_lo + blockIdx.y) * C::TY);
 }
 
-// tiles of the frame around the interior block (walls, wrap, partial tiles)
-__host__ __device__ inline void edge_tile(int e, int ntx, int a_lo, int a_hi, int b_lo, int b_hi, int &a, int &b) {
-  const int bottom = ntx * b_lo;
-  if (e < bottom) {
-    a = e % ntx;
-    b = e / ntx;
-    return;
-  }
-  e -= bottom;
-  const int side = ntx - (a_hi - a_lo);
-  const int mid = side * (b_hi - b_lo);
-  if (e < mid) {
-    b = b_lo + e / side;
-    const int c = e % side;
-    a = c < a_lo ? c : a_hi + (c - a_lo);
-    return;
-  }
-  e -= mid;
-  a = e % ntx;
-  b = b_hi + e / ntx;
-}
+// tiles of the frame around the interior block (walls, wrap, partial tiles):
+// edge_tile in lbs_tiles.h
 
 // With SPLIT, a frame tile of CPT nodes per thread is processed as CPT
 // tiles of one node per thread by CPT blocks.  On a small lattice the frame
@@ -815,18 +738,6 @@ inline void fork_end(const StepPtrs &S, cudaStream_t st, bool on) {
   cudaStreamWaitEvent(st, S.fork->join, 0);
 }
 
-// interior tile range [a_lo, a_hi) x [b_lo, b_hi): R2 of the tile and the
-// streaming sources of R2 (a 3-node frame) stay clear of the walls and of the
-// lattice end.  Empty ranges are normalised to (0, 0).
-inline void interior_range(int nx, int ny, int TX, int TY, int &a_lo, int &a_hi, int &b_lo, int &b_hi) {
-  a_lo = (3 + TX - 1) / TX;
-  a_hi = (nx - 3 - TX) >= 0 ? (nx - 3 - TX) / TX + 1 : 0;
-  b_lo = (3 + TY - 1) / TY;
-  b_hi = (ny - 3 - TY) >= 0 ? (ny - 3 - TY) / TY + 1 : 0;
-  if (a_hi <= a_lo) a_lo = a_hi = 0;
-  if (b_hi <= b_lo) b_lo = b_hi = 0;
-}
-
 template <class C>
 int step_kernel_count(const Params &P) {
   const int ntx = (P.nx + C::TX - 1) / C::TX, nty = (P.ny + C::TY - 1) / C::TY;
@@ -855,13 +766,14 @@ cudaError_t launch_step(const Params &P, const StepPtrs &S, cudaStream_t st) {
 // A persistent-style walk over a tile table spanning many lattices of
 // different sizes: block i takes tiles i, i + grid, ...  Each tile runs the
 // same step_tile code as the single-lattice kernels, on its lattice's buffers
-// chosen by the parity of that lattice's iteration counter.
+// chosen by the parity of that lattice's iteration k + it (k: its iteration at
+// the start of the chunk, it: this launch's place in the chunk).
 // SPLIT (frame tiles only): each table tile is run as CPT tiles of one node
 // per thread.
 template <class C, bool EDGE, bool LIN = false, bool SPLIT = false>
 __global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) batch_step_kernel(const BatchLattice *lats,
                                                                                   const BatchTile *tiles, int ntiles,
-                                                                                  int *err) {
+                                                                                  int it, int *err) {
   using H = typename FrameCfg<C, SPLIT>::type;
   constexpr int parts = C::TY / H::TY;
   __shared__ Params sP;
@@ -871,10 +783,10 @@ __global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) batch_step_kerne
     if (threadIdx.x == 0) {
       const BatchTile T = tiles[t / parts];
       const BatchLattice &L = lats[T.lat];
-      skip = L.k >= L.kend;
+      skip = L.k + it >= L.kend;
       if (!skip) {
         sP = L.P;
-        const int p = (int)(L.k & 1);
+        const int p = (int)((L.k + it) & 1);
         sS.g_in = L.g[p];
         sS.g_out = L.g[p ^ 1];
         sS.u_in = L.u[p];
@@ -882,7 +794,7 @@ __global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) batch_step_kerne
         sS.b_in = L.b[p];
         sS.b_out = L.b[p ^ 1];
         sS.kptr = &lats[T.lat].k;
-        sS.koff = 0;
+        sS.koff = it;
         sS.tm_g = sS.tm_u = nullptr;
         sS.err = err;
         sS.fork = nullptr;
@@ -897,14 +809,11 @@ __global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) batch_step_kerne
   }
 }
 
-static __global__ void batch_advance_kernel(BatchLattice *lats, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && lats[i].k < lats[i].kend) lats[i].k += 1;
-}
-
+// launch `it` of a chunk: the interior tiles and the frame tiles of every
+// unfinished lattice at its iteration k + it
 template <class C>
 cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
-                              int ne, const BatchTile *edge_lin, int nl, int *err, cudaStream_t st,
+                              int ne, const BatchTile *edge_lin, int nl, int it, int *err, cudaStream_t st,
                               const StreamFork *fork) {
   // resident blocks of the persistent kernel on this device (computed once;
   // the initialisation of a function-local static is thread-safe)
@@ -933,27 +842,27 @@ cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *in
     if constexpr (C::CPT >= 2) {
       if (ne + nl <= sms) {
         using H = typename FrameCfg<C, true>::type;
-        if (ne > 0) batch_step_kernel<C, true, false, true><<<C::CPT * ne, H::NT, 0, fs>>>(lats, edge, ne, err);
-        if (nl > 0) batch_step_kernel<C, true, true, true><<<C::CPT * nl, H::NT, 0, fs>>>(lats, edge_lin, nl, err);
+        if (ne > 0) batch_step_kernel<C, true, false, true><<<C::CPT * ne, H::NT, 0, fs>>>(lats, edge, ne, it, err);
+        if (nl > 0)
+          batch_step_kernel<C, true, true, true><<<C::CPT * nl, H::NT, 0, fs>>>(lats, edge_lin, nl, it, err);
         return;
       }
     }
-    if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, err);
+    if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, it, err);
     if (nl > 0)
-      batch_step_kernel<C, true, true><<<nl < blocks ? nl : blocks, C::NT, 0, fs>>>(lats, edge_lin, nl, err);
+      batch_step_kernel<C, true, true><<<nl < blocks ? nl : blocks, C::NT, 0, fs>>>(lats, edge_lin, nl, it, err);
   };
   if (split) {
     cudaEventRecord(fork->fork, st);
     cudaStreamWaitEvent(fork->side, fork->fork, 0);
     frame(fork->side);
   }
-  if (ni > 0) batch_step_kernel<C, false><<<ni < blocks ? ni : blocks, C::NT, 0, st>>>(lats, interior, ni, err);
+  if (ni > 0) batch_step_kernel<C, false><<<ni < blocks ? ni : blocks, C::NT, 0, st>>>(lats, interior, ni, it, err);
   if (!split) frame(st);
   if (split) {
     cudaEventRecord(fork->join, fork->side);
     cudaStreamWaitEvent(st, fork->join, 0);
   }
-  if (nlats > 0) batch_advance_kernel<<<(nlats + 127) / 128, 128, 0, st>>>(lats, nlats);
   return cudaGetLastError();
 }
 
@@ -1004,26 +913,135 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int c0,
 // bound on mbarrier polls (each try_wait also suspends in hardware for a while)
 constexpr uint32_t kMaxPolls = 1u << 22;
 
+// (box geometry in lbs_tiles.h: TmaGeom)
 template <class C>
-struct TmaCfg {
+struct TmaCfg : TmaGeom<C::TX, C::TY, (int)sizeof(typename C::gs), (int)sizeof(typename C::us)> {
+  using B = TmaGeom<C::TX, C::TY, (int)sizeof(typename C::gs), (int)sizeof(typename C::us)>;
   using gs = typename C::gs;
   using us = typename C::us;
   using real = typename C::real;
-  static constexpr int TX = C::TX, TY = C::TY;
-  static constexpr int ALIGN = 16 / (int)sizeof(gs);        // elements per 16 bytes
-  static constexpr int XO = ((3 + ALIGN - 1) / ALIGN) * ALIGN;  // smem column of node x0
-  static constexpr int GW = ((XO + TX + 3 + ALIGN - 1) / ALIGN) * ALIGN;  // box width
-  static constexpr int GH = TY + 6;                           // rows y0-3 .. y0+TY+2
-  static constexpr int UW = TX + 4, UH = TY + 4;              // u on R2
+  static constexpr int TX = C::TX, TY = C::TY, GW = B::GW, GH = B::GH, UW = B::UW, UH = B::UH, XO = B::XO;
   static constexpr int UEL = (int)(sizeof(us) / sizeof(real)); // reals per u record (2 or 4)
   static constexpr size_t G_BYTES = (size_t)9 * GH * GW * sizeof(gs);
   static constexpr size_t U_BYTES = (size_t)UH * UW * sizeof(us);
   static constexpr size_t N_BYTES = (size_t)4 * (TY + 2) * (TX + 2) * sizeof(real);
+  // N on R1 overwrites the u box once every thread has read its taps when it
+  // fits there (FP32 and FP16 storage: float N, 16-byte u records); FP64 has
+  // its own N array
+  static constexpr bool N_IN_U = N_BYTES <= U_BYTES;
   static constexpr size_t OFF_U = (G_BYTES + 127) / 128 * 128;
-  static constexpr size_t OFF_N = OFF_U + (U_BYTES + 127) / 128 * 128;
-  static constexpr size_t OFF_BAR = OFF_N + (N_BYTES + 15) / 16 * 16;
+  static constexpr size_t OFF_N = N_IN_U ? OFF_U : OFF_U + (U_BYTES + 127) / 128 * 128;
+  static constexpr size_t OFF_BAR = N_IN_U ? OFF_U + (U_BYTES + 15) / 16 * 16 : OFF_N + (N_BYTES + 15) / 16 * 16;
   static constexpr size_t SMEM = OFF_BAR + 16;
 };
+
+// Phases 1-3 of a TMA-staged interior tile at (x0, y0) whose g box (sg) and
+// u box (su) have landed: u(t+dt) on R2 in place, N on R1 into snb, then
+// streaming from the g box, source, collision and the stores.  With
+// TmaCfg::N_IN_U, snb is the u box itself: every thread computes its N
+// entries into registers and keeps its own nodes' u for the store, and the
+// entries are written once all threads have read their u taps.
+template <class C>
+__device__ __forceinline__ void tma_tile(const Params &P, const StepPtrs &S, const typename C::gs *sg,
+                                         typename C::us *su, typename C::real *snb, int x0, int y0) {
+  using T = TmaCfg<C>;
+  using R = typename C::real;
+  using us = typename C::us;
+  using gs = typename C::gs;
+  // g is held in units of g * 2^gshift (1 unless FP16 storage)
+  const R inv = gscale_inv<gs, R>(P), scl = gscale<gs, R>(P);
+  const R kap = (R)P.kappa * inv;
+  auto G = [&](int q, int r, int c) -> R {
+    const gs v = sg[((size_t)q * T::GH + r) * T::GW + c];
+    if constexpr (sizeof(gs) == 2) return __half2float(v);
+    else return (R)v;
+  };
+  // phase 1: u(t+dt) on R2, in place (R2 position (cx, cy) = node (x0-2+cx, y0-2+cy);
+  // its g row is cy+1, its g column cx+XO-2)
+  for (int e = threadIdx.x; e < T::UW * T::UH; e += C::NT) {
+    const int cx = e % T::UW, cy = e / T::UW;
+    const int gr = cy + 1, gc = cx + T::XO - 2;
+    R p[9], o[9];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) {
+      p[q] = G(q, gr - ey(q), gc - ex(q));
+      o[q] = G(q, gr, gc);
+    }
+    // first moments of own and streamed populations, as gather() forms them
+    R gx, gy, fx, fy;
+    first_moment(o, gx, gy);
+    first_moment(p, fx, fy);
+    su[e] = uadd(su[e], kap * (gx + fx), kap * (gy + fy));
+  }
+  __syncthreads();
+  // phase 2: N on R1
+  constexpr int W1 = C::TX + 2, H1 = C::TY + 2, NE = W1 * H1, NPER = (NE + C::NT - 1) / C::NT;
+  const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
+  const R hdx = R(0.5) * (R)P.inv_dx;
+  // own nodes' u(t+dt), read before N may overwrite the box
+  us uown[C::CPT];
+#pragma unroll
+  for (int i = 0; i < C::CPT; ++i) uown[i] = su[(ty + i * C::NTY + 2) * T::UW + (tx + 2)];
+  {
+    const R lam = (R)P.lam, mu = (R)P.mu;
+    R nreg[T::N_IN_U ? NPER : 1][4];
+#pragma unroll
+    for (int k = 0; k < NPER; ++k) {
+      const int e = threadIdx.x + k * C::NT;
+      if (e >= NE) break;
+      const int rx = e % W1, ry = e / W1;
+      const int c = (ry + 1) * T::UW + (rx + 1);
+      R dxx, dxy, dyx, dyy, H[4], N[4];
+      udiff(su[c + 1], su[c - 1], dxx, dxy);
+      udiff(su[c + T::UW], su[c - T::UW], dyx, dyy);
+      H[0] = dxx * hdx;
+      H[1] = dyx * hdx;
+      H[2] = dxy * hdx;
+      H[3] = dyy * hdx;
+      material<R>(P, lam, mu, H, N);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if constexpr (T::N_IN_U) nreg[k][m] = N[m];
+        else snb[(m * H1 + ry) * W1 + rx] = N[m];
+      }
+    }
+    if constexpr (T::N_IN_U) {
+      __syncthreads();  // every u tap has been read: N may overwrite the box
+#pragma unroll
+      for (int k = 0; k < NPER; ++k) {
+        const int e = threadIdx.x + k * C::NT;
+        if (e >= NE) break;
+        const int rx = e % W1, ry = e / W1;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) snb[(m * H1 + ry) * W1 + rx] = nreg[k][m];
+      }
+    }
+  }
+  __syncthreads();
+  // phase 3: stream again from shared memory, source, collision, store
+  const size_t plane = (size_t)P.ny * P.pitch;
+  const R omega = (R)P.omega, sigma = (R)P.sigma;
+  const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
+  gs *__restrict__ go = (gs *)S.g_out;
+  us *__restrict__ uo = (us *)S.u_out;
+#pragma unroll
+  for (int i = 0; i < C::CPT; ++i) {
+    const int lx = tx, ly = ty + i * C::NTY;
+    const int gr = ly + 3, gc = lx + T::XO;
+    R f[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = G(q, gr - ey(q), gc - ex(q));
+    const int rx = lx + 1, ry = ly + 1;
+    auto n = [&](int m, int yy, int xx) -> R { return snb[(m * H1 + yy) * W1 + xx]; };
+    const R Sx = fmr(n(0, ry, rx + 1) - n(0, ry, rx - 1), hdx, (n(1, ry + 1, rx) - n(1, ry - 1, rx)) * hdx) + sbx;
+    const R Sy = fmr(n(2, ry, rx + 1) - n(2, ry, rx - 1), hdx, (n(3, ry + 1, rx) - n(3, ry - 1, rx)) * hdx) + sby;
+    collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
+    const size_t idx = (size_t)(y0 + ly) * P.pitch + (x0 + lx);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[q], scl);
+    uo[idx] = uown[i];
+  }
+}
 
 template <class C>
 __global__ void __launch_bounds__(C::NT) step_tma_kernel(const Params P, const StepPtrs S,
@@ -1060,78 +1078,7 @@ __global__ void __launch_bounds__(C::NT) step_tma_kernel(const Params P, const S
     return;
   }
 
-  // g is held in units of g * 2^gshift (1 unless FP16 storage)
-  const R inv = gscale_inv<typename C::gs, R>(P), scl = gscale<typename C::gs, R>(P);
-  const R kap = (R)P.kappa * inv;
-  auto G = [&](int q, int r, int c) -> R {
-    const gs v = sg[((size_t)q * T::GH + r) * T::GW + c];
-    if constexpr (sizeof(gs) == 2) return __half2float(v);
-    else return (R)v;
-  };
-  // phase 1: u(t+dt) on R2, in place (R2 position (cx, cy) = node (x0-2+cx, y0-2+cy);
-  // its g row is cy+1, its g column cx+XO-2)
-  for (int e = threadIdx.x; e < T::UW * T::UH; e += C::NT) {
-    const int cx = e % T::UW, cy = e / T::UW;
-    const int gr = cy + 1, gc = cx + T::XO - 2;
-    R p[9], o[9];
-#pragma unroll
-    for (int q = 1; q < 9; ++q) {
-      p[q] = G(q, gr - ey(q), gc - ex(q));
-      o[q] = G(q, gr, gc);
-    }
-    // same grouping as gather(): first moments of own and streamed populations
-    const R gx = (o[1] - o[3]) + (o[5] - o[6]) + (o[8] - o[7]);
-    const R gy = (o[2] - o[4]) + (o[5] - o[8]) + (o[6] - o[7]);
-    const R fx = (p[1] - p[3]) + (p[5] - p[6]) + (p[8] - p[7]);
-    const R fy = (p[2] - p[4]) + (p[5] - p[8]) + (p[6] - p[7]);
-    su[e] = uadd(su[e], kap * (gx + fx), kap * (gy + fy));
-  }
-  __syncthreads();
-  // phase 2: N on R1
-  {
-    const R lam = (R)P.lam, mu = (R)P.mu, hdx = R(0.5) * (R)P.inv_dx;
-    constexpr int W1 = C::TX + 2, H1 = C::TY + 2;
-    for (int e = threadIdx.x; e < W1 * H1; e += C::NT) {
-      const int rx = e % W1, ry = e / W1;
-      const int c = (ry + 1) * T::UW + (rx + 1);
-      R dxx, dxy, dyx, dyy, H[4], N[4];
-      udiff(su[c + 1], su[c - 1], dxx, dxy);
-      udiff(su[c + T::UW], su[c - T::UW], dyx, dyy);
-      H[0] = dxx * hdx;
-      H[1] = dyx * hdx;
-      H[2] = dxy * hdx;
-      H[3] = dyy * hdx;
-      material<R>(P, lam, mu, H, N);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) snb[(m * H1 + ry) * W1 + rx] = N[m];
-    }
-  }
-  __syncthreads();
-  // phase 3: stream again from shared memory, source, collision, store
-  const size_t plane = (size_t)P.ny * P.pitch;
-  const R omega = (R)P.omega, sigma = (R)P.sigma, hdx = R(0.5) * (R)P.inv_dx;
-  const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
-  gs *__restrict__ go = (gs *)S.g_out;
-  us *__restrict__ uo = (us *)S.u_out;
-  constexpr int W1 = C::TX + 2, H1 = C::TY + 2;
-  const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
-#pragma unroll
-  for (int i = 0; i < C::CPT; ++i) {
-    const int lx = tx, ly = ty + i * C::NTY;
-    const int gr = ly + 3, gc = lx + T::XO;
-    R f[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) f[q] = G(q, gr - ey(q), gc - ex(q));
-    const int rx = lx + 1, ry = ly + 1;
-    auto n = [&](int m, int yy, int xx) -> R { return snb[(m * H1 + yy) * W1 + xx]; };
-    const R Sx = (n(0, ry, rx + 1) - n(0, ry, rx - 1)) * hdx + (n(1, ry + 1, rx) - n(1, ry - 1, rx)) * hdx + sbx;
-    const R Sy = (n(2, ry, rx + 1) - n(2, ry, rx - 1)) * hdx + (n(3, ry + 1, rx) - n(3, ry - 1, rx)) * hdx + sby;
-    collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
-    const size_t idx = (size_t)(y0 + ly) * P.pitch + (x0 + lx);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[q], scl);
-    uo[idx] = su[(ly + 2) * T::UW + (lx + 2)];
-  }
+  tma_tile<C>(P, S, sg, su, snb, x0, y0);
 }
 
 template <class C>
@@ -1159,9 +1106,11 @@ cudaError_t launch_step_tma(const Params &P, const StepPtrs &S, cudaStream_t st)
 template <class C>
 struct Tma2Cfg {
   using T = TmaCfg<C>;
-  static constexpr size_t STAGE = T::OFF_N;  // g and u of one tile (128-aligned)
+  // g and u of one tile (128-aligned); N in the u box of the stage, or in one
+  // array after both stages
+  static constexpr size_t STAGE = T::OFF_U + (T::U_BYTES + 127) / 128 * 128;
   static constexpr size_t OFF_N = 2 * STAGE;
-  static constexpr size_t OFF_BAR = OFF_N + (T::N_BYTES + 15) / 16 * 16;
+  static constexpr size_t OFF_BAR = T::N_IN_U ? OFF_N : OFF_N + (T::N_BYTES + 15) / 16 * 16;
   static constexpr size_t SMEM = OFF_BAR + 32;
 };
 
@@ -1187,7 +1136,6 @@ __global__ void __launch_bounds__(C::NT) step_tma2_kernel(const Params P, const 
   using us = typename C::us;
   using gs = typename C::gs;
   extern __shared__ __align__(128) unsigned char dsm[];
-  R *snb = (R *)(dsm + T2::OFF_N);
   uint64_t *bar = (uint64_t *)(dsm + T2::OFF_BAR);  // bar[0], bar[1]
   auto tile_xy = [&](int t, int &x0, int &y0) {
     x0 = (a_lo + t % ni) * C::TX;
@@ -1204,16 +1152,6 @@ __global__ void __launch_bounds__(C::NT) step_tma2_kernel(const Params P, const 
     }
   }
   __syncthreads();
-  const R inv = gscale_inv<typename C::gs, R>(P), scl = gscale<typename C::gs, R>(P);
-  const R kap = (R)P.kappa * inv;
-  const size_t plane = (size_t)P.ny * P.pitch;
-  const R omega = (R)P.omega, sigma = (R)P.sigma, hdx = R(0.5) * (R)P.inv_dx;
-  const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
-  const R lam = (R)P.lam, mu = (R)P.mu;
-  gs *__restrict__ go = (gs *)S.g_out;
-  us *__restrict__ uo = (us *)S.u_out;
-  constexpr int W1 = C::TX + 2, H1 = C::TY + 2;
-  const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
 
   for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
     const int s = i & 1;
@@ -1248,62 +1186,7 @@ __global__ void __launch_bounds__(C::NT) step_tma2_kernel(const Params P, const 
     }
     int x0, y0;
     tile_xy(t, x0, y0);
-    auto G = [&](int q, int r, int c) -> R {
-      const gs v = sg[((size_t)q * T::GH + r) * T::GW + c];
-      if constexpr (sizeof(gs) == 2) return __half2float(v);
-      else return (R)v;
-    };
-    // phase 1: u(t+dt) on R2, in place
-    for (int e = threadIdx.x; e < T::UW * T::UH; e += C::NT) {
-      const int cx = e % T::UW, cy = e / T::UW;
-      const int gr = cy + 1, gc = cx + T::XO - 2;
-      R p[9], o[9];
-#pragma unroll
-      for (int q = 1; q < 9; ++q) {
-        p[q] = G(q, gr - ey(q), gc - ex(q));
-        o[q] = G(q, gr, gc);
-      }
-      const R gx = (o[1] - o[3]) + (o[5] - o[6]) + (o[8] - o[7]);
-      const R gy = (o[2] - o[4]) + (o[5] - o[8]) + (o[6] - o[7]);
-      const R fx = (p[1] - p[3]) + (p[5] - p[6]) + (p[8] - p[7]);
-      const R fy = (p[2] - p[4]) + (p[5] - p[8]) + (p[6] - p[7]);
-      su[e] = uadd(su[e], kap * (gx + fx), kap * (gy + fy));
-    }
-    __syncthreads();
-    // phase 2: N on R1
-    for (int e = threadIdx.x; e < W1 * H1; e += C::NT) {
-      const int rx = e % W1, ry = e / W1;
-      const int c = (ry + 1) * T::UW + (rx + 1);
-      R dxx, dxy, dyx, dyy, H[4], N[4];
-      udiff(su[c + 1], su[c - 1], dxx, dxy);
-      udiff(su[c + T::UW], su[c - T::UW], dyx, dyy);
-      H[0] = dxx * hdx;
-      H[1] = dyx * hdx;
-      H[2] = dxy * hdx;
-      H[3] = dyy * hdx;
-      material<R>(P, lam, mu, H, N);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) snb[(m * H1 + ry) * W1 + rx] = N[m];
-    }
-    __syncthreads();
-    // phase 3: stream, source, collision, store
-#pragma unroll
-    for (int j = 0; j < C::CPT; ++j) {
-      const int lx = tx, ly = ty + j * C::NTY;
-      const int gr = ly + 3, gc = lx + T::XO;
-      R f[9];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) f[q] = G(q, gr - ey(q), gc - ex(q));
-      const int rx = lx + 1, ry = ly + 1;
-      auto n = [&](int m, int yy, int xx) -> R { return snb[(m * H1 + yy) * W1 + xx]; };
-      const R Sx = (n(0, ry, rx + 1) - n(0, ry, rx - 1)) * hdx + (n(1, ry + 1, rx) - n(1, ry - 1, rx)) * hdx + sbx;
-      const R Sy = (n(2, ry, rx + 1) - n(2, ry, rx - 1)) * hdx + (n(3, ry + 1, rx) - n(3, ry - 1, rx)) * hdx + sby;
-      collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
-      const size_t idx = (size_t)(y0 + ly) * P.pitch + (x0 + lx);
-#pragma unroll
-      for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[q], scl);
-      uo[idx] = su[(ly + 2) * T::UW + (lx + 2)];
-    }
+    tma_tile<C>(P, S, sg, su, T::N_IN_U ? (R *)su : (R *)(dsm + T2::OFF_N), x0, y0);
     __syncthreads();  // this stage is free for the prefetch after next
   }
 }
@@ -1340,6 +1223,274 @@ cudaError_t launch_step_tma2(const Params &P, const StepPtrs &S, cudaStream_t st
   if (!beside) launch_edge<C>(P, S, nedge, ntx, a_lo, a_hi, b_lo, b_hi, st);
   fork_end(S, st, beside);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ two iterations per launch
+// Temporal blocking on periodic lattices: a block advances its output tile
+// by two iterations, k -> k + 2, from g_k on the tile plus 6 nodes and u_k on
+// the tile plus 5, both staged in shared memory (Fuse2Geom in lbs_tiles.h).
+// First iteration over the enlarged region: u_{k+1} on tile + 5, N on tile
+// + 4, g_{k+1} on tile + 3 (rounded to the storage type into a second shared
+// g array, exactly as a single iteration stores it); second iteration on the
+// tile: u_{k+2} on tile + 2, N on tile + 1, g_{k+2} on the tile.  Each node's
+// arithmetic is that of the single-iteration kernels, so two fused
+// iterations equal two single ones bitwise.  DRAM traffic per node update is
+// half of one iteration's; the halo regions are recomputed (about 1.3x the
+// arithmetic).  Interior tiles (tile + 6 inside the lattice) stage by TMA;
+// the frame tiles gather their boxes with wrapped loads.
+template <class C>
+struct Fuse2Cfg : Fuse2Geom<C::TX, C::TY, (int)sizeof(typename C::gs), (int)sizeof(typename C::us)> {
+  using B = Fuse2Geom<C::TX, C::TY, (int)sizeof(typename C::gs), (int)sizeof(typename C::us)>;
+  using gs = typename C::gs;
+  using us = typename C::us;
+  using real = typename C::real;
+  static constexpr int UEL = (int)(sizeof(us) / sizeof(real));
+  static constexpr size_t G_BYTES = (size_t)9 * B::GH * B::GW * sizeof(gs);
+  static constexpr size_t U_BYTES = (size_t)B::UH * B::UW * sizeof(us);
+  static constexpr size_t H_BYTES = (size_t)9 * B::HH * B::HW * sizeof(gs);
+  static constexpr size_t N_BYTES = (size_t)4 * B::NH * B::NW * sizeof(real);
+  static constexpr size_t OFF_U = (G_BYTES + 127) / 128 * 128;
+  static constexpr size_t OFF_H = OFF_U + (U_BYTES + 127) / 128 * 128;
+  static constexpr size_t OFF_N = OFF_H + (H_BYTES + 15) / 16 * 16;
+  static constexpr size_t OFF_BAR = OFF_N + (N_BYTES + 15) / 16 * 16;
+  static constexpr size_t SMEM = OFF_BAR + 16;
+};
+
+template <class G>
+__device__ __forceinline__ typename G::real fconv(typename G::gs v) {
+  if constexpr (sizeof(typename G::gs) == 2) return __half2float(v);
+  else return (typename G::real)v;
+}
+template <class G>
+__device__ __forceinline__ typename G::gs fstore(typename G::real v) {
+  if constexpr (sizeof(typename G::gs) == 2) return __float2half_rn(v);
+  else return (typename G::gs)v;
+}
+
+// both iterations of one tile from its staged boxes; stores the nodes of the
+// tile that lie in the lattice
+template <class C>
+__device__ __forceinline__ void fused2_tile(const Params &P, const StepPtrs &S, const typename C::gs *sg,
+                                            typename C::us *su, typename C::gs *sh, typename C::real *sn, int x0,
+                                            int y0) {
+  using F = Fuse2Cfg<C>;
+  using R = typename C::real;
+  using us = typename C::us;
+  using gs = typename C::gs;
+  const R inv = gscale_inv<gs, R>(P), scl = gscale<gs, R>(P);
+  const R kap = (R)P.kappa * inv, hdx = R(0.5) * (R)P.inv_dx;
+  const R lam = (R)P.lam, mu = (R)P.mu, omega = (R)P.omega, sigma = (R)P.sigma;
+  const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
+  // u(t+dt) at node offset (i, j) from the populations of array A (g box or g1)
+  auto advance_u = [&](auto A, int i, int j) {
+    R p[9], o[9];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) {
+      p[q] = A(q, i - ex(q), j - ey(q));
+      o[q] = A(q, i, j);
+    }
+    R gx, gy, fx, fy;
+    first_moment(o, gx, gy);
+    first_moment(p, fx, fy);
+    us &uu = su[F::u(i, j)];
+    uu = uadd(uu, kap * (gx + fx), kap * (gy + fy));
+  };
+  // N at node offset (i, j) from u in the u box
+  auto stress = [&](int i, int j) {
+    R dxx, dxy, dyx, dyy, H[4], N[4];
+    udiff(su[F::u(i + 1, j)], su[F::u(i - 1, j)], dxx, dxy);
+    udiff(su[F::u(i, j + 1)], su[F::u(i, j - 1)], dyx, dyy);
+    H[0] = dxx * hdx;
+    H[1] = dyx * hdx;
+    H[2] = dxy * hdx;
+    H[3] = dyy * hdx;
+    material<R>(P, lam, mu, H, N);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) sn[F::n(m, i, j)] = N[m];
+  };
+  // streamed populations of node (i, j) from array A, collided with S = div N
+  auto collide_at = [&](auto A, int i, int j, R f[9]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = A(q, i - ex(q), j - ey(q));
+    auto n = [&](int m, int ii, int jj) -> R { return sn[F::n(m, ii, jj)]; };
+    const R Sx = fmr(n(0, i + 1, j) - n(0, i - 1, j), hdx, (n(1, i, j + 1) - n(1, i, j - 1)) * hdx) + sbx;
+    const R Sy = fmr(n(2, i + 1, j) - n(2, i - 1, j), hdx, (n(3, i, j + 1) - n(3, i, j - 1)) * hdx) + sby;
+    collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
+  };
+  auto Gk = [&](int q, int i, int j) -> R { return fconv<F>(sg[F::g(q, i, j)]); };
+  auto G1 = [&](int q, int i, int j) -> R { return fconv<F>(sh[F::h(q, i, j)]); };
+
+  // first iteration: u_{k+1} on tile + 5, N on tile + 4, g_{k+1} on tile + 3
+  for (int e = threadIdx.x; e < F::UW * F::UH; e += C::NT) advance_u(Gk, e % F::UW - 5, e / F::UW - 5);
+  __syncthreads();
+  for (int e = threadIdx.x; e < F::NW * F::NH; e += C::NT) stress(e % F::NW - 4, e / F::NW - 4);
+  __syncthreads();
+  for (int e = threadIdx.x; e < F::HW * F::HH; e += C::NT) {
+    const int i = e % F::HW - 3, j = e / F::HW - 3;
+    R f[9];
+    collide_at(Gk, i, j, f);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sh[F::h(q, i, j)] = fstore<F>(f[q]);
+  }
+  __syncthreads();
+  // second iteration: u_{k+2} on tile + 2, N on tile + 1, g_{k+2} on the tile
+  constexpr int W2 = C::TX + 4, W1 = C::TX + 2;
+  for (int e = threadIdx.x; e < W2 * (C::TY + 4); e += C::NT) advance_u(G1, e % W2 - 2, e / W2 - 2);
+  __syncthreads();
+  for (int e = threadIdx.x; e < W1 * (C::TY + 2); e += C::NT) stress(e % W1 - 1, e / W1 - 1);
+  __syncthreads();
+  const size_t plane = (size_t)P.ny * P.pitch;
+  gs *__restrict__ go = (gs *)S.g_out;
+  us *__restrict__ uo = (us *)S.u_out;
+  const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
+#pragma unroll
+  for (int c = 0; c < C::CPT; ++c) {
+    const int i = tx, j = ty + c * C::NTY;
+    R f[9];
+    collide_at(G1, i, j, f);
+    const int x = x0 + i, y = y0 + j;
+    if (x >= P.nx || y >= P.ny) continue;
+    const size_t idx = (size_t)y * P.pitch + x;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[q], scl);
+    uo[idx] = su[F::u(i, j)];
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::NT) step_fused2_tma_kernel(const Params P, const StepPtrs S,
+                                                                const __grid_constant__ CUtensorMap tm_g,
+                                                                const __grid_constant__ CUtensorMap tm_u, int a_lo,
+                                                                int b_lo) {
+  using F = Fuse2Cfg<C>;
+  using gs = typename C::gs;
+  using us = typename C::us;
+  using R = typename C::real;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  gs *sg = (gs *)dsm;
+  us *su = (us *)(dsm + F::OFF_U);
+  gs *sh = (gs *)(dsm + F::OFF_H);
+  R *sn = (R *)(dsm + F::OFF_N);
+  uint64_t *bar = (uint64_t *)(dsm + F::OFF_BAR);
+  const int x0 = (a_lo + blockIdx.x) * C::TX, y0 = (b_lo + blockIdx.y) * C::TY;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, (uint32_t)(F::G_BYTES + F::U_BYTES));
+    tma_load_3d(sg, &tm_g, x0 - F::XO, y0 - 6, 0, bar);
+    tma_load_2d(su, &tm_u, F::UEL * (x0 - 5), y0 - 5, bar);
+  }
+  __syncthreads();  // the barrier is initialised before anyone polls it
+  int ok = 0;
+  for (uint32_t i = 0; i < kMaxPolls; ++i)
+    if (mbar_try_wait(bar, 0)) {
+      ok = 1;
+      break;
+    }
+  if (!__syncthreads_and(ok)) {
+    if (threadIdx.x == 0 && S.err) atomicExch(S.err, 1);
+    return;
+  }
+  fused2_tile<C>(P, S, sg, su, sh, sn, x0, y0);
+}
+
+// frame tiles of a periodic lattice: the boxes gathered with wrapped loads
+template <class C>
+__global__ void __launch_bounds__(C::NT) step_fused2_edge_kernel(const Params P, const StepPtrs S, int ntx, int a_lo,
+                                                                 int a_hi, int b_lo, int b_hi) {
+  using F = Fuse2Cfg<C>;
+  using gs = typename C::gs;
+  using us = typename C::us;
+  using R = typename C::real;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  gs *sg = (gs *)dsm;
+  us *su = (us *)(dsm + F::OFF_U);
+  gs *sh = (gs *)(dsm + F::OFF_H);
+  R *sn = (R *)(dsm + F::OFF_N);
+  int a, b;
+  edge_tile(blockIdx.x, ntx, a_lo, a_hi, b_lo, b_hi, a, b);
+  const int x0 = a * C::TX, y0 = b * C::TY;
+  const gs *__restrict__ g = (const gs *)S.g_in;
+  const us *__restrict__ u = (const us *)S.u_in;
+  const size_t plane = (size_t)P.ny * P.pitch;
+  // the used columns of the g box: node offsets -6 .. TX + 5
+  constexpr int GU = C::TX + 12;
+  for (int e = threadIdx.x; e < 9 * F::GH * GU; e += C::NT) {
+    const int q = e / (F::GH * GU), r = e % (F::GH * GU);
+    const int i = r % GU - 6, j = r / GU - 6;
+    int x = x0 + i, y = y0 + j;
+    locate(P, x, y);
+    sg[F::g(q, i, j)] = g[q * plane + (size_t)y * P.pitch + x];
+  }
+  for (int e = threadIdx.x; e < F::UW * F::UH; e += C::NT) {
+    const int i = e % F::UW - 5, j = e / F::UW - 5;
+    int x = x0 + i, y = y0 + j;
+    locate(P, x, y);
+    su[e] = u[(size_t)y * P.pitch + x];
+  }
+  __syncthreads();
+  fused2_tile<C>(P, S, sg, su, sh, sn, x0, y0);
+}
+
+// Fused iterations apply to lattices with every edge periodic and both sides
+// at least 16 nodes (a tile's read region then wraps at most once); other
+// lattices advance one iteration per call.
+inline bool fused2_applies(const Params &P) { return P.per_x && P.per_y && P.nx >= 16 && P.ny >= 16; }
+
+template <class C>
+cudaError_t launch_step_fused2(const Params &P, const StepPtrs &S, cudaStream_t st) {
+  using F = Fuse2Cfg<C>;
+  const int ntx = (P.nx + C::TX - 1) / C::TX, nty = (P.ny + C::TY - 1) / C::TY;
+  int a_lo, a_hi, b_lo, b_hi;
+  interior_range_m(P.nx, P.ny, C::TX, C::TY, 6, a_lo, a_hi, b_lo, b_hi);
+  const int ni = a_hi - a_lo, nj = b_hi - b_lo;
+  if (ni > 0 && nj > 0 && (!S.tm_g || !S.tm_u)) return cudaErrorInvalidValue;
+  const int nedge = ntx * nty - ni * nj;
+  const bool beside = fork_begin(S, st, ni > 0 && nj > 0 && nedge > 0);
+  cudaStream_t es = beside ? S.fork->side : st;
+  if (nedge > 0) step_fused2_edge_kernel<C><<<nedge, C::NT, F::SMEM, es>>>(P, S, ntx, a_lo, a_hi, b_lo, b_hi);
+  if (ni > 0 && nj > 0)
+    step_fused2_tma_kernel<C><<<dim3(ni, nj), C::NT, F::SMEM, st>>>(P, S, *(const CUtensorMap *)S.tm_g,
+                                                                      *(const CUtensorMap *)S.tm_u, a_lo, b_lo);
+  fork_end(S, st, beside);
+  return cudaGetLastError();
+}
+
+template <class C>
+bool make_fused2_maps(const Params &P, const void *g, const void *u, void *out_g, void *out_u) {
+  using F = Fuse2Cfg<C>;
+  using gs = typename C::gs;
+  using R = typename C::real;
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }();
+  if (!encode) return false;
+  const CUtensorMapDataType gt = sizeof(gs) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : sizeof(gs) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const cuuint64_t gdim[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.ny, 9};
+  const cuuint64_t gstr[2] = {(cuuint64_t)P.pitch * sizeof(gs), (cuuint64_t)P.ny * P.pitch * sizeof(gs)};
+  const cuuint32_t gbox[3] = {(cuuint32_t)F::GW, (cuuint32_t)F::GH, 9};
+  const cuuint32_t est[3] = {1, 1, 1};
+  CUresult r1 = encode((CUtensorMap *)out_g, gt, 3, const_cast<void *>(g), gdim, gstr, gbox, est,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUtensorMapDataType ut = sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t udim[2] = {(cuuint64_t)F::UEL * P.pitch, (cuuint64_t)P.ny};
+  const cuuint64_t ustr[1] = {(cuuint64_t)F::UEL * P.pitch * sizeof(R)};
+  const cuuint32_t ubox[2] = {(cuuint32_t)(F::UEL * F::UW), (cuuint32_t)F::UH};
+  CUresult r2 = encode((CUtensorMap *)out_u, ut, 2, const_cast<void *>(u), udim, ustr, ubox, est,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return false;
+  return cudaFuncSetAttribute(step_fused2_tma_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(step_fused2_edge_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)F::SMEM) == cudaSuccess;
 }
 
 // ------------------------------------------------------------------ row-marching strips
@@ -1449,10 +1600,9 @@ __global__ void __launch_bounds__(M::NT) step_march_kernel(const Params P, const
         p[q] = G(q, row - ey(q), gc - ex(q));
         o[q] = G(q, row, gc);
       }
-      const R gx = (o[1] - o[3]) + (o[5] - o[6]) + (o[8] - o[7]);
-      const R gy = (o[2] - o[4]) + (o[5] - o[8]) + (o[6] - o[7]);
-      const R fx = (p[1] - p[3]) + (p[5] - p[6]) + (p[8] - p[7]);
-      const R fy = (p[2] - p[4]) + (p[5] - p[8]) + (p[6] - p[7]);
+      R gx, gy, fx, fy;
+      first_moment(o, gx, gy);
+      first_moment(p, fx, fy);
       us &uu = U(row, cx);
       uu = uadd(uu, kap * (gx + fx), kap * (gy + fy));
     }
@@ -1525,8 +1675,8 @@ __global__ void __launch_bounds__(M::NT) step_march_kernel(const Params P, const
       R f[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) f[q] = G(q, row - ey(q), gc - ex(q));
-      const R Sx = (N(0, row, rx + 1) - N(0, row, rx - 1)) * hdx + (N(1, row + 1, rx) - N(1, row - 1, rx)) * hdx + sbx;
-      const R Sy = (N(2, row, rx + 1) - N(2, row, rx - 1)) * hdx + (N(3, row + 1, rx) - N(3, row - 1, rx)) * hdx + sby;
+      const R Sx = fmr(N(0, row, rx + 1) - N(0, row, rx - 1), hdx, (N(1, row + 1, rx) - N(1, row - 1, rx)) * hdx) + sbx;
+      const R Sy = fmr(N(2, row, rx + 1) - N(2, row, rx - 1), hdx, (N(3, row + 1, rx) - N(3, row - 1, rx)) * hdx) + sby;
       collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
       const size_t idx = (size_t)row * P.pitch + (x0 + lx);
 #pragma unroll
@@ -1730,12 +1880,9 @@ __global__ void __launch_bounds__(C::NT) fields_kernel(const Params P, const typ
       Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
       Sx += (R)(P.rho0 * P.body[0]);
       Sy += (R)(P.rho0 * P.body[1]);
-      R m1x = 0, m1y = 0;
-      for (int q = 1; q < 9; ++q) {
-        const R gq = gload(g, q * plane + idx, inv);
-        m1x += R(ex(q)) * gq;
-        m1y += R(ey(q)) * gq;
-      }
+      R gq[9], m1x, m1y;
+      for (int q = 1; q < 9; ++q) gq[q] = gload(g, q * plane + idx, inv);
+      first_moment(gq, m1x, m1y);
       const double hdt = 0.5 * P.dt;
       vo[2 * o] = (P.c * (double)(m1x * inv) - hdt * (double)Sx) / P.rho0;
       vo[2 * o + 1] = (P.c * (double)(m1y * inv) - hdt * (double)Sy) / P.rho0;

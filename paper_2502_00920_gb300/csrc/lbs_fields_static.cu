@@ -20,7 +20,39 @@ static __device__ __align__(256) double g_fields_stage[kStageDoubles];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_stage_mu;
+// the array's device address per device, with the identifier of the context
+// it was looked up in: a device reset destroys that context (and the address
+// with it), and the next call looks the address up again in the new one
 double *g_stage_ptr[kMaxDevices] = {};
+unsigned long long g_stage_ctx[kMaxDevices] = {};
+
+// unique identifier of the calling thread's current context (0 if unknown);
+// identifiers are never reused within a process
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static const GetCurrent get_current = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return (GetCurrent)fn;
+  }();
+  static const GetId get_id = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return (GetId)fn;
+  }();
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 // u, v, P of rows [y_lo, y_hi) into dense row-block arrays (x fastest)
 template <class C>
@@ -51,12 +83,9 @@ __global__ void __launch_bounds__(C::NT) fields_rows_kernel(const Params P, cons
       Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
       Sx += (R)(P.rho0 * P.body[0]);
       Sy += (R)(P.rho0 * P.body[1]);
-      R m1x = 0, m1y = 0;
-      for (int q = 1; q < 9; ++q) {
-        const R gq = gload(g, q * plane + idx, inv);
-        m1x += R(ex(q)) * gq;
-        m1y += R(ey(q)) * gq;
-      }
+      R gq[9], m1x, m1y;
+      for (int q = 1; q < 9; ++q) gq[q] = gload(g, q * plane + idx, inv);
+      first_moment(gq, m1x, m1y);
       const double hdt = 0.5 * P.dt;
       // g is held in units of g * 2^gshift (1 unless FP16 storage)
       vo[2 * o] = (P.c * (double)(m1x * inv) - hdt * (double)Sx) / P.rho0;
@@ -111,9 +140,12 @@ extern "C" int lbs_fields_static(lbs_handle *h, double *u, double *v, double *P)
     set_error("lbs_fields_static: no usable current device");
     return LBS_ECUDA;
   }
-  if (!g_stage_ptr[dev]) {
+  // (cudaGetDevice does not create the context; the address lookup below
+  // does, so the identifier is taken after it on the first call)
+  const unsigned long long ctx = current_context_id();
+  if (!g_stage_ptr[dev] || ctx == 0 || ctx != g_stage_ctx[dev]) {
     // the array's name is a host-side stand-in; its device address is looked
-    // up once per device, with that device current
+    // up once per device (and context), with that device current
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_fields_stage);
     if (e != cudaSuccess || !p) {
@@ -121,8 +153,18 @@ extern "C" int lbs_fields_static(lbs_handle *h, double *u, double *v, double *P)
       return LBS_ECUDA;
     }
     g_stage_ptr[dev] = (double *)p;
+    g_stage_ctx[dev] = current_context_id();
   }
   double *stage = g_stage_ptr[dev];
+  // an error after the first launch leaves earlier blocks' copies queued:
+  // wait for them while the lock is still held, so that the next call cannot
+  // overwrite the array under them and no host buffer is written after the
+  // return
+  auto fail_queued = [&](const std::string &msg) {
+    cudaStreamSynchronize(h->stream);
+    set_error(msg);
+    return LBS_ECUDA;
+  };
   const int rows = (int)(kStageDoubles / per_row);
   for (int y_lo = 0; y_lo < ny; y_lo += rows) {
     const int y_hi = y_lo + rows < ny ? y_lo + rows : ny;
@@ -138,10 +180,7 @@ extern "C" int lbs_fields_static(lbs_handle *h, double *u, double *v, double *P)
     else
       le = launch_rows<F16>(h->P, h->g[h->parity], h->u[h->parity], y_lo, y_hi, u ? su : nullptr, v ? sv : nullptr,
                             P ? sp : nullptr, h->stream);
-    if (le != cudaSuccess) {
-      set_error(std::string("lbs_fields_static: launch: ") + cudaGetErrorString(le));
-      return LBS_ECUDA;
-    }
+    if (le != cudaSuccess) return fail_queued(std::string("lbs_fields_static: launch: ") + cudaGetErrorString(le));
     h->launches += 1;
     // the next block's kernel follows these copies on the same stream
     if ((u && cudaMemcpyAsync(u + (size_t)2 * y_lo * nx, su, 2 * n * sizeof(double), cudaMemcpyDeviceToHost,
@@ -149,10 +188,8 @@ extern "C" int lbs_fields_static(lbs_handle *h, double *u, double *v, double *P)
         (v && cudaMemcpyAsync(v + (size_t)2 * y_lo * nx, sv, 2 * n * sizeof(double), cudaMemcpyDeviceToHost,
                               h->stream) != cudaSuccess) ||
         (P && cudaMemcpyAsync(P + (size_t)4 * y_lo * nx, sp, 4 * n * sizeof(double), cudaMemcpyDeviceToHost,
-                              h->stream) != cudaSuccess)) {
-      set_error("lbs_fields_static: copy to host failed");
-      return LBS_ECUDA;
-    }
+                              h->stream) != cudaSuccess))
+      return fail_queued("lbs_fields_static: copy to host failed");
   }
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
     set_error(std::string("lbs_fields_static: ") + cudaGetErrorString(e));

@@ -7,10 +7,9 @@
 #include <string>
 
 #include "../../include/lbs.h"
+#include "lbs_tiles.h"
 
 namespace lbs {
-
-enum { kLeft = 0, kRight = 1, kBottom = 2, kTop = 3 };
 
 // Per-lattice parameters handed to every kernel by value.  Everything the
 // kernels need to know about one lattice: geometry, material, boundary
@@ -70,9 +69,15 @@ struct TileShape {
 struct BatchLattice {
   Params P;
   void *g[2], *u[2], *b[2];
-  int64_t k;     // iteration of the state in buffers [k & 1]; advanced on the device
+  int64_t k;     // iteration at the start of the current chunk (launch `it` of the
+                 // chunk steps iteration k + it, buffers [(k + it) & 1]); advanced
+                 // on the device once per chunk (launch_batch_advance)
   int64_t kend;  // the lattice stops here (its tiles return at once)
 };
+
+// advance every lattice's chunk-start iteration by a chunk of n launches
+// (to its end at most); one launch
+cudaError_t launch_batch_advance(BatchLattice *lats, int nlats, int n, cudaStream_t st);
 
 // One tile of a batch: lattice index and tile coordinates (in tiles).
 struct BatchTile {
@@ -89,8 +94,16 @@ struct Launchers {
   int default_variant;
   TileShape (*shape)(int variant);
   const char *(*name)(int variant);  // the interior kernel of a variant, e.g. "step_tma_kernel"
+  // one call of a variant: iterations_per_call iterations (2 for the fused
+  // two-iteration variant on lattices it applies to, else 1), buffers s.*_in ->
+  // s.*_out; kernels_per_step counts the kernels of one call
   cudaError_t (*step)(const Params &p, const StepPtrs &s, int variant, cudaStream_t st);
   int (*kernels_per_step)(const Params &p, int variant);
+  int (*iterations_per_call)(const Params &p, int variant);
+  // exactly one iteration whatever the variant (global-memory tiles; the
+  // last iteration of an odd count under a fused variant); one or two kernels
+  cudaError_t (*step1)(const Params &p, const StepPtrs &s, cudaStream_t st);
+  int (*kernels_per_step1)(const Params &p);
   // TMA descriptors of one (g, u) buffer pair for a tile variant; returns
   // false if the variant does not use TMA.  out_g/out_u: CUtensorMap storage.
   bool (*tma_maps)(const Params &p, int variant, const void *g, const void *u, void *out_g, void *out_u);
@@ -101,14 +114,15 @@ struct Launchers {
   cudaError_t (*monitor)(const Params &p, const void *g, const void *u, double *partials, int nblocks,
                          double *out7, int64_t k, cudaStream_t st);
   cudaError_t (*probe)(const Params &p, const void *u, const int32_t *idx, int n, double *out, cudaStream_t st);
-  // one iteration of every unfinished lattice of a batch: interior tiles,
-  // frame tiles, frame tiles of the lattices with two-point wall
-  // extrapolation (their own kernel), then the per-lattice counters (tile
-  // shape of the default global-memory variant, batch_tile())
+  // launch `it` of a chunk: one iteration of every unfinished lattice of a
+  // batch, each at its iteration k + it (k: its iteration at the start of the
+  // chunk): interior tiles, frame tiles, frame tiles of the lattices with
+  // two-point wall extrapolation (their own kernel); tile shape of the
+  // default global-memory variant, batch_tile
   // (`fork`, if given, runs the frame tiles on its side stream, concurrently
-  // with the interior tiles; the counters advance after both)
+  // with the interior tiles; both have finished when the next launch starts)
   cudaError_t (*batch_step)(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
-                            int ne, const BatchTile *edge_lin, int nl, int *err, cudaStream_t st,
+                            int ne, const BatchTile *edge_lin, int nl, int it, int *err, cudaStream_t st,
                             const StreamFork *fork);
   TileShape batch_tile;
   size_t g_elem, u_elem, b_elem;  // bytes per stored g value, per u record, per boundary entry

@@ -20,6 +20,24 @@
 using lbs::BatchLattice;
 using lbs::BatchTile;
 
+namespace lbs {
+
+// every lattice's chunk-start iteration advances by the chunk's n launches,
+// to its end at most
+static __global__ void batch_advance_kernel(BatchLattice *lats, int nlats, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nlats) return;
+  const int64_t k = lats[i].k, kend = lats[i].kend;
+  if (k < kend) lats[i].k = k + n < kend ? k + n : kend;
+}
+
+cudaError_t launch_batch_advance(BatchLattice *lats, int nlats, int n, cudaStream_t st) {
+  if (nlats > 0 && n > 0) batch_advance_kernel<<<(nlats + 127) / 128, 128, 0, st>>>(lats, nlats, n);
+  return cudaGetLastError();
+}
+
+}  // namespace lbs
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -181,11 +199,11 @@ cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int nres, int ni, 
   auto direct = [&]() -> cudaError_t {
     for (int64_t it = 0; it < n; ++it) {
       const BatchTile *t = s->d_tiles;
-      const cudaError_t e =
-          L.batch_step(s->d_lats, nres, t, ni, t + ni, ne, t + ni + ne, nl, s->d_err, s->stream, &s->fork);
+      const cudaError_t e = L.batch_step(s->d_lats, nres, t, ni, t + ni, ne, t + ni + ne, nl, (int)it, s->d_err,
+                                         s->stream, &s->fork);
       if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return lbs::launch_batch_advance(s->d_lats, nres, (int)n, s->stream);
   };
   if (n != s->cfg.chunk || n < 2) return direct();
   if (!G.warm) {
@@ -342,7 +360,7 @@ void run(lbs_server *s) {
     for (Req *r : res) longest = std::max(longest, r->nsteps - r->k);
     chunk = std::min(chunk, longest);
     const double tb = s->now();
-    const int64_t launched = chunk * ((ni > 0) + (ne > 0) + (nl > 0) + 1);
+    const int64_t launched = chunk * ((ni > 0) + (ne > 0) + (nl > 0)) + 1;
     cudaError_t e = run_chunk(s, L, (int)res.size(), ni, ne, nl, chunk, graph);
     const cudaError_t es = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = es;

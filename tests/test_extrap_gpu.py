@@ -98,6 +98,15 @@ def test_tile_variants_agree_bitwise_with_linear_extrapolation(L, precision):
         assert all(np.array_equal(a, b) for a, b in zip(got, ref)), v
 
 
+# Under the linear reading this block (24 x 16, every edge Neumann, nu 0.2)
+# is not neutral: its one-iteration map grows perturbations by 1.5 % per
+# iteration, 19x over the 200 iterations of the test (the spectral radius is
+# pinned in tests/test_stability_spectrum.py), so the rounding of the reduced
+# precisions arrives amplified by that much; the own reading grows them by 3 %
+# in all.  FP64 rounding stays far below its bar either way.
+LINEAR_BLOCK_GROWTH = 20.0
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6), ("fp16s", 1e-2)])
 @pytest.mark.parametrize("model", ["svk", "nh"])
 def test_homogeneous_stress_is_static_with_linear_extrapolation(L, oracle_mod, model, precision, tol):
@@ -107,8 +116,9 @@ def test_homogeneous_stress_is_static_with_linear_extrapolation(L, oracle_mod, m
     case, u0, P = homogeneous_case(I, oracle_mod, model, "linear")
     u, v, Pf = run_gpu(L, case.replace(precision=precision), 200, u0, None)
     scale = np.abs(u0).max()
-    assert np.abs(u - u0).max() <= tol * scale
-    assert np.abs(Pf - P.reshape(4)).max() <= tol * 5 * np.abs(P).max()
+    bar = tol * (1.0 if precision == "fp64" else LINEAR_BLOCK_GROWTH)
+    assert np.abs(u - u0).max() <= bar * scale
+    assert np.abs(Pf - P.reshape(4)).max() <= bar * 5 * np.abs(P).max()
 
 
 def test_bending_wave_blows_up_at_the_oracles_iteration(L, oracle_mod):

@@ -35,12 +35,14 @@ ERRORS = {}
 
 @pytest.fixture(scope="module", autouse=True)
 def _error_report():
-    """Write every measured error to gpurun_out/parity_errors.json (or the
-    directory in LBS_ERROR_REPORT) for the record."""
+    """With LBS_ERROR_REPORT set to a directory, write every measured error
+    to parity_errors.json there (for the record); otherwise write nothing."""
     yield
     import json
     import os
-    out = os.environ.get("LBS_ERROR_REPORT", "gpurun_out")
+    out = os.environ.get("LBS_ERROR_REPORT")
+    if not out:
+        return
     try:
         os.makedirs(out, exist_ok=True)
         with open(os.path.join(out, "parity_errors.json"), "w") as f:
@@ -169,6 +171,26 @@ def test_tile_variants_agree_bitwise(L, precision):
     for o in outs[1:]:
         for x, y in zip(outs[0], o):
             assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("steps,chunk", [(61, 0), (64, 16), (131, 64)])
+def test_fused_iterations_equal_single_ones_bitwise(L, oracle_mod, steps, chunk):
+    """The two-iterations-per-launch variant (periodic lattices) computes
+    every node with the single-iteration arithmetic: equal bitwise to the
+    default variant over even and odd iteration counts, direct launches and
+    graphs, on lattices with ragged tiles and frame tiles; and it matches the
+    oracle at the FP64 bar's FP32 counterpart."""
+    fused = next(v for v in range(len(L.tile_variants("fp32"))) if L.tile_variant_name("fp32", v) ==
+                 "step_fused2_tma_kernel")
+    for nx, ny in ((130, 90), (256, 100), (40, 40)):
+        case = I.Case("f", nx, ny, 0, model="nh", nu=0.3, precision="fp32", edges=(I.PERIODIC,) * 4)
+        u0, v0 = rnd(case)
+        a = run_gpu(L, case, steps, u0, v0, graph_chunk=chunk)
+        b = run_gpu(L, case, steps, u0, v0, graph_chunk=chunk, variant=fused)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y), (nx, ny)
+    ur = run_oracle(oracle_mod, case, steps, u0, v0)[0]
+    assert rel(b[0], ur) <= TOL["fp32"]
 
 
 def test_monitor_matches_oracle(L, oracle_mod):

@@ -93,12 +93,20 @@ def test_admission_respects_budget(L):
 
 
 def test_continuous_admission(L):
-    """Requests arriving while others are on the GPU join the running batch."""
+    """Requests arriving while others are on the GPU join the running batch,
+    their work overlaps on the device with the lattice already resident, and
+    every result, the late arrivals' included, equals the same lattice run
+    alone, bitwise."""
     # stable over its whole history in the oracle (finite to beyond 7000
     # iterations; the same load at nu = 0.3 and peak 0.2 goes non-finite
     # between 1000 and 2000 iterations)
-    long = I.tension(512, 256, 6500, ramp=500, model="nh", nu=0.2, peak=0.05)
-    short = [I.tension(64, 48, 200, ramp=50, model="svk", nu=0.1) for _ in range(4)]
+    long = I.tension(512, 256, 6500, ramp=500, model="nh", nu=0.2, peak=0.05, precision="fp32")
+    trac = I.Edge("neumann", "linear_ramp", (0.01, 0.0), 0, 80)
+    short = [I.tension(64, 48, 200, ramp=50, model="svk", nu=0.1, precision="fp32"),
+             I.shear(96, 260, model="nh", nu=0.2, gamma=0.05, ramp=300, precision="fp32"),
+             I.Case("late_m", 130, 70, 300, model="svk", nu=0.2, edges=(I.CLAMPED, trac, I.FREE, I.FREE),
+                    precision="fp32"),
+             I.cantilever(200, 24, 150, width=60, amp=0.01, nu=0.25, precision="fp32")]
     with L.Server(precision="fp32", chunk=32) as srv:
         t_long = srv.submit(long)
         t_wait = time.time()
@@ -111,11 +119,15 @@ def test_continuous_admission(L):
         srv.drain(120)
         il = srv.poll(t_long)
         infos = [srv.poll(t) for t in ts]
-        for t in [t_long] + ts:
-            assert srv.result(t)[3] == L.OK
+        results = [srv.result(t) for t in [t_long] + ts]
     # the short ones were admitted and finished while the long one was running
+    assert all(il["t_admit"] < i["t_submit"] for i in infos)
     assert all(i["t_admit"] < il["t_done"] for i in infos)
     assert all(i["t_done"] < il["t_done"] for i in infos)
+    for case, (u, v, P, rc) in zip([long] + short, results):
+        assert rc == L.OK, case.name
+        ua, va, Pa = alone(L, case)
+        assert np.array_equal(u, ua) and np.array_equal(v, va) and np.array_equal(P, Pa), case.name
 
 
 def test_failures_reported_per_ticket(L):
