@@ -215,6 +215,21 @@ int lbs_probe(lbs_handle *h, int32_t n, const int32_t *idx, double *out);
 /* Run the monitor reduction now (synchronous). */
 int lbs_monitor(lbs_handle *h, lbs_monitors *out);
 
+/* Grid error norms of the current displacement u against a reference field
+ * u_ref (Sect. 4, Eq. griderror): with du = u - u_ref over the n = nx * ny
+ * nodes, ||a||_2 = sqrt(sum_nodes a . a) and ||a||_inf = max over nodes of
+ * max(|a_1|, |a_2|),
+ *   out[0] = E2   = ||du||_2 / (n ||u_ref||_2),
+ *   out[1] = Einf = ||du||_inf / ||u_ref||_2
+ * (the norm in the denominators is the reference's).  u_ref: caller-owned,
+ * [ny][nx][2] doubles like lbs_fields' u; lbs_grid_error takes it in host
+ * memory (staged in the idle state buffers; a temporary only if they cannot
+ * hold it), lbs_grid_error_device in device memory.  A deterministic
+ * reduction on the handle's stream; synchronous.  LBS_EINVAL for null
+ * arguments. */
+int lbs_grid_error(lbs_handle *h, const double *u_ref, double out[2]);
+int lbs_grid_error_device(lbs_handle *h, const double *u_ref, double out[2]);
+
 /* Monitor every m iterations inside lbs_step (0 disables; default 1000).
  * A non-finite value makes later lbs_step / lbs_sync calls return
  * LBS_EUNSTABLE. */

@@ -6,10 +6,10 @@
  * number of iterations) share one GPU.  A worker thread admits queued
  * requests while their device footprint (lbs_footprint) fits the HBM budget,
  * keeps the admitted lattices' state resident, and advances all of them
- * together: every iteration is one launch of a batched kernel that walks a
- * tile table spanning all resident lattices (interior tiles, then frame
- * tiles) and one launch that advances their iteration counters.  The worker
- * runs `chunk` iterations between scheduling points; a lattice that reaches
+ * together: every iteration launches batched kernels that walk tile tables
+ * spanning all resident lattices (interior tiles, frame tiles), and once per
+ * chunk one launch advances their iteration counters.  The worker runs `chunk`
+ * iterations between scheduling points; a lattice that reaches
  * its iteration count stops (its tiles return at once), is checked for
  * non-finite values, has u, v and P copied to host memory owned by the server
  * and its device memory released, after which queued requests are admitted.
@@ -29,6 +29,14 @@
  * swapped out unless the waiting request then fits.
  * Each lattice computes exactly what lbs_step computes for it alone, with
  * either wall reading (lbs_lattice.wall_extrap) and any mix of the two.
+ *
+ * Batch tile shapes (no counterpart in the paper).  The batched kernels come
+ * in the four global-memory tile shapes of lbs_tile_variants (0..3), which
+ * compute every node with the same operations.  Unless batch_shape fixes
+ * one, the worker times them: a trial runs one chunk on each shape (real
+ * work, not a rehearsal) and keeps the one with the most node updates per
+ * second of device time; a new trial starts when the resident node count has
+ * moved by a quarter since the last.  Results do not depend on the shape.
  *
  * The server owns its device memory and its results until lbs_result hands
  * them over.  All functions are thread-safe.
@@ -51,6 +59,8 @@ typedef struct {
   int32_t max_resident;  /* cap on resident lattices (0: none)                          */
   int32_t queue_limit;   /* lbs_submit returns LBS_EBUSY beyond this many queued (0: none) */
   double preempt_after_s; /* > 0: preemption, below (0: never; < 0: LBS_EINVAL)           */
+  int32_t batch_shape;   /* 0: batch tile shape picked by timing, below; k >= 1: always
+                            shape k - 1 (lbs_tile_variants' global-memory tiles 0..3)    */
 } lbs_server_config;
 
 enum { LBS_TICKET_QUEUED = 0, LBS_TICKET_RUNNING = 1, LBS_TICKET_DONE = 2, LBS_TICKET_FAILED = 3 };
@@ -76,6 +86,9 @@ typedef struct {
   size_t hbm_budget;
   int64_t launches;       /* kernels launched by the worker                    */
   int64_t preemptions;    /* lattices swapped out to host memory               */
+  int32_t batch_shape;    /* current batch tile shape (0..3)                   */
+  int32_t batch_tx, batch_ty; /* its nodes along x and y                       */
+  int64_t batch_tunings;  /* completed timing trials of the shapes             */
 } lbs_server_stats;
 
 /* Start a server on the current CUDA device.  Errors: LBS_EINVAL (bad

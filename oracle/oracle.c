@@ -660,6 +660,35 @@ void ora_step(ora_sim *s, long nsteps) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* grid error norms (Sect. 4, Eq. griderror and the grid norms beside it)    */
+
+/* ||a||_2 = sqrt(sum over nodes of a . a), a = [n][2] */
+static double grid_norm2(long n, const double *a) {
+  double s = 0.0;
+  for (long i = 0; i < n; ++i) s += a[2 * i] * a[2 * i] + a[2 * i + 1] * a[2 * i + 1];
+  return sqrt(s);
+}
+
+/* ||a||_inf = max over nodes of max(|a_1|, |a_2|) (reading of max(u1, u2)) */
+static double grid_norm_inf(long n, const double *a) {
+  double m = 0.0;
+  for (long i = 0; i < n; ++i) {
+    double v = fabs(a[2 * i]) > fabs(a[2 * i + 1]) ? fabs(a[2 * i]) : fabs(a[2 * i + 1]);
+    if (v > m) m = v;
+  }
+  return m;
+}
+
+void ora_grid_error(long n, const double *u, const double *u_ref, double out[2]) {
+  double *du = malloc(sizeof(double) * 2 * n);
+  for (long i = 0; i < 2 * n; ++i) du[i] = u[i] - u_ref[i];
+  double r = grid_norm2(n, u_ref);
+  out[0] = (1.0 / (double)n) * grid_norm2(n, du) / r;
+  out[1] = grid_norm_inf(n, du) / r;
+  free(du);
+}
+
+/* ------------------------------------------------------------------------ */
 /* the carried state (for the stability analysis of the one-step map)       */
 
 long ora_state_size(const ora_sim *s) { return 21 * s->n; }

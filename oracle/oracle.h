@@ -106,6 +106,11 @@ void ora_equilibrium(double cs, double r, const double j[2], const double Pi[4],
 void ora_forcing(double cs, const double S[2], double psi[9]);
 void ora_gradient(const ora_config *cfg, const double *u, double *H);
 void ora_load(const ora_config *cfg, int edge, long k, double out[2]);
+/* Grid error norms of Sect. 4 (Eq. griderror): E2 = (1/n) ||u - u_ref||_2 /
+ * ||u_ref||_2 and Einf = ||u - u_ref||_inf / ||u_ref||_2 over n nodes, u and
+ * u_ref [n][2]; ||a||_2 = sqrt(sum a . a), ||a||_inf = max of max(|a_1|, |a_2|)
+ * (the reference's norm in the denominators). */
+void ora_grid_error(long n, const double *u, const double *u_ref, double out[2]);
 /* A node value a[y*nx + x] carried to the wall(s) (wx: ORA_LEFT/ORA_RIGHT or
  * -1, wy: ORA_BOTTOM/ORA_TOP or -1) a boundary link crosses, as the Neumann
  * rule of Sect. 3.3 takes r, the Pi entries and P + Pi(H) under cfg->extrap;

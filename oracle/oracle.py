@@ -79,6 +79,7 @@ def lib():
         L.ora_forcing.argtypes = [ctypes.c_double, _dp, _dp]
         L.ora_gradient.argtypes = [ctypes.POINTER(_Config), _dp, _dp]
         L.ora_load.argtypes = [ctypes.POINTER(_Config), ctypes.c_int, ctypes.c_long, _dp]
+        L.ora_grid_error.argtypes = [ctypes.c_long, _dp, _dp, _dp]
         L.ora_wall_value.restype = ctypes.c_double
         L.ora_wall_value.argtypes = [ctypes.POINTER(_Config), _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int]
@@ -233,3 +234,13 @@ def wall_value(case, a, x: int, y: int, xwall=None, ywall=None) -> float:
     a = _f64(a, (case.ny, case.nx))
     return float(lib().ora_wall_value(ctypes.byref(config(case)), _ptr(a), int(x), int(y), WALL[xwall],
                                       WALL[ywall]))
+
+
+def grid_error(u, u_ref):
+    """(E2, Einf) of Eq. griderror for fields [..., 2] of the same shape."""
+    u = _f64(u)
+    r = _f64(u_ref)
+    assert u.shape == r.shape and u.shape[-1] == 2
+    out = np.empty(2)
+    lib().ora_grid_error(u.size // 2, _ptr(u), _ptr(r), _ptr(out))
+    return float(out[0]), float(out[1])

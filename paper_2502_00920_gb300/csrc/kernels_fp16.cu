@@ -74,6 +74,20 @@ bool tma_maps(const Params &p, int v, const void *g, const void *u, void *og, vo
   return make_tma_maps<V4>(p, g, u, og, ou);
 }
 
+// the server's batch tile shapes: the global-memory tiles V0-V3
+constexpr int kBatchShapes = 4;
+TileShape batch_shape(int b) { return shape(b); }
+cudaError_t batch_step(int b, BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
+                       int ne, const BatchTile *edge_lin, int nl, int it, int *err, cudaStream_t st,
+                       const StreamFork *fork) {
+  switch (b) {
+    case 1: return launch_batch_step<V1>(lats, nlats, interior, ni, edge, ne, edge_lin, nl, it, err, st, fork);
+    case 2: return launch_batch_step<V2>(lats, nlats, interior, ni, edge, ne, edge_lin, nl, it, err, st, fork);
+    case 3: return launch_batch_step<V3>(lats, nlats, interior, ni, edge, ne, edge_lin, nl, it, err, st, fork);
+    default: return launch_batch_step<V0>(lats, nlats, interior, ni, edge, ne, edge_lin, nl, it, err, st, fork);
+  }
+}
+
 const Launchers kL = {kVariants,
                       (1 << 4) | (1 << 5) | (1 << 6) | (1 << 7),
                       7,  // default: the fastest on the 16384^2 roofline lattice
@@ -89,8 +103,10 @@ const Launchers kL = {kVariants,
                       launch_fields<V0>,
                       launch_monitor<V0>,
                       launch_probe<V0>,
-                      launch_batch_step<V0>,
-                      {V0::TX, V0::TY},
+                      launch_grid_error<V0>,
+                      batch_step,
+                      kBatchShapes,
+                      batch_shape,
                       sizeof(typename P::gs),
                       sizeof(typename P::us),
                       sizeof(typename P::real)};

@@ -713,6 +713,40 @@ int lbs_probe(lbs_handle *h, int32_t n, const int32_t *idx, double *out) {
   return rc;
 }
 
+int lbs_grid_error_device(lbs_handle *h, const double *u_ref, double out[2]) {
+  if (!h || !u_ref || !out) return fail(LBS_EINVAL, "null argument");
+  // the monitors' partials (5 per block) hold the 3 per block needed here
+  LBS_CK(h->L->grid_error(h->P, h->u[h->parity], u_ref, h->mon_partials, monitor_blocks(h->P), h->mon_out,
+                          h->stream));
+  h->launches += 2;
+  double o[3];
+  LBS_CK(cudaMemcpyAsync(o, h->mon_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LBS_CK(cudaStreamSynchronize(h->stream));
+  out[0] = o[0];
+  out[1] = o[1];
+  return LBS_OK;
+}
+
+int lbs_grid_error(lbs_handle *h, const double *u_ref, double out[2]) {
+  if (!h || !u_ref || !out) return fail(LBS_EINVAL, "null argument");
+  const size_t bytes = (size_t)h->P.nx * h->P.ny * 2 * sizeof(double);
+  // stage the reference field in the buffers of the other parity (the next
+  // iteration overwrites them unread), else in a temporary
+  Scratch sc = scratch_of(h, h->parity ^ 1);
+  double *dev = scratch_take(sc, bytes);
+  const bool owned = dev == nullptr;
+  if (owned && !(dev = (double *)dev_alloc(h->alloc, bytes, h->stream))) return fail(LBS_ENOMEM, "reference buffer");
+  int rc = LBS_OK;
+  if (cudaMemcpyAsync(dev, u_ref, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    rc = fail(LBS_ECUDA, "reference copy");
+  if (!rc) rc = lbs_grid_error_device(h, dev, out);
+  if (owned) {
+    cudaStreamSynchronize(h->stream);
+    dev_free(h->alloc, dev, h->stream);
+  }
+  return rc;
+}
+
 int lbs_monitor(lbs_handle *h, lbs_monitors *out) {
   if (!h || !out) return fail(LBS_EINVAL, "null argument");
   int rc = launch_monitor_async(h);

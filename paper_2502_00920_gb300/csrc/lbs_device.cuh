@@ -1987,6 +1987,69 @@ static __global__ void monitor_final_kernel(const double *partials, int nblocks,
   }
 }
 
+// Grid error norms of Sect. 4 (Eq. griderror) against a reference field
+// u_ref [ny][nx][2]: per-block partials of sum |u - u_ref|^2, max over nodes
+// of max(|du_1|, |du_2|) and sum |u_ref|^2 (warp shuffle, then the block),
+// then a fixed-order final pass: out = {E2, Einf, ||u_ref||_2} with
+// E2 = ||du||_2 / (n ||u_ref||_2), Einf = ||du||_inf / ||u_ref||_2.
+template <class C>
+__global__ void __launch_bounds__(kMonThreads) grid_error_kernel(const Params P, const typename C::us *u,
+                                                                 const double *uref, double *partials) {
+  const size_t n = (size_t)P.nx * P.ny;
+  double d2 = 0, dmax = 0, r2 = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % P.nx), y = (int)(i / P.nx);
+    const double2 uv = u_value(u[(size_t)y * P.pitch + x]);
+    const double rx = uref[2 * i], ry = uref[2 * i + 1];
+    const double dx = uv.x - rx, dy = uv.y - ry;
+    d2 += dx * dx + dy * dy;
+    dmax = fmax(dmax, fmax(fabs(dx), fabs(dy)));
+    r2 += rx * rx + ry * ry;
+  }
+  __shared__ double sh[3][kMonThreads / 32];
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  d2 = warp_sum(d2);
+  dmax = warp_max(dmax);
+  r2 = warp_sum(r2);
+  if (lane == 0) {
+    sh[0][w] = d2;
+    sh[1][w] = dmax;
+    sh[2][w] = r2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double o[3] = {0, 0, 0};
+    for (int j = 0; j < kMonThreads / 32; ++j) {
+      o[0] += sh[0][j];
+      o[1] = fmax(o[1], sh[1][j]);
+      o[2] += sh[2][j];
+    }
+    for (int m = 0; m < 3; ++m) partials[(size_t)blockIdx.x * 3 + m] = o[m];
+  }
+}
+
+static __global__ void grid_error_final_kernel(const double *partials, int nblocks, double nodes, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double d2 = 0, dmax = 0, r2 = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    d2 += partials[(size_t)b * 3 + 0];
+    dmax = fmax(dmax, partials[(size_t)b * 3 + 1]);
+    r2 += partials[(size_t)b * 3 + 2];
+  }
+  const double rn = sqrt(r2);
+  out[0] = sqrt(d2) / (nodes * rn);
+  out[1] = dmax / rn;
+  out[2] = rn;
+}
+
+template <class C>
+cudaError_t launch_grid_error(const Params &P, const void *u, const double *uref, double *partials, int nblocks,
+                              double *out3, cudaStream_t st) {
+  grid_error_kernel<C><<<nblocks, kMonThreads, 0, st>>>(P, (const typename C::us *)u, uref, partials);
+  grid_error_final_kernel<<<1, 32, 0, st>>>(partials, nblocks, (double)P.nx * P.ny, out3);
+  return cudaGetLastError();
+}
+
 template <class C>
 __global__ void probe_kernel(const Params P, const typename C::us *u, const int32_t *idx, int n, double *out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -114,17 +114,22 @@ struct Launchers {
   cudaError_t (*monitor)(const Params &p, const void *g, const void *u, double *partials, int nblocks,
                          double *out7, int64_t k, cudaStream_t st);
   cudaError_t (*probe)(const Params &p, const void *u, const int32_t *idx, int n, double *out, cudaStream_t st);
+  // grid error norms against a device reference field (out3: E2, Einf, ||u_ref||_2)
+  cudaError_t (*grid_error)(const Params &p, const void *u, const double *uref, double *partials, int nblocks,
+                            double *out3, cudaStream_t st);
   // launch `it` of a chunk: one iteration of every unfinished lattice of a
   // batch, each at its iteration k + it (k: its iteration at the start of the
   // chunk): interior tiles, frame tiles, frame tiles of the lattices with
-  // two-point wall extrapolation (their own kernel); tile shape of the
-  // default global-memory variant, batch_tile
+  // two-point wall extrapolation (their own kernel), on tiles of batch shape
+  // `shape` (0 .. nbatch_shapes - 1, global-memory tiles; every shape computes
+  // each node with the same operations, so a server may switch between them)
   // (`fork`, if given, runs the frame tiles on its side stream, concurrently
   // with the interior tiles; both have finished when the next launch starts)
-  cudaError_t (*batch_step)(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
-                            int ne, const BatchTile *edge_lin, int nl, int it, int *err, cudaStream_t st,
-                            const StreamFork *fork);
-  TileShape batch_tile;
+  cudaError_t (*batch_step)(int shape, BatchLattice *lats, int nlats, const BatchTile *interior, int ni,
+                            const BatchTile *edge, int ne, const BatchTile *edge_lin, int nl, int it, int *err,
+                            cudaStream_t st, const StreamFork *fork);
+  int nbatch_shapes;
+  TileShape (*batch_shape)(int shape);
   size_t g_elem, u_elem, b_elem;  // bytes per stored g value, per u record, per boundary entry
 };
 

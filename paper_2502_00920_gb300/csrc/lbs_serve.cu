@@ -194,13 +194,13 @@ struct ChunkGraph {
   }
 };
 
-cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int nres, int ni, int ne, int nl, int64_t n,
+cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int shape, int nres, int ni, int ne, int nl, int64_t n,
                       ChunkGraph &G) {
   auto direct = [&]() -> cudaError_t {
     for (int64_t it = 0; it < n; ++it) {
       const BatchTile *t = s->d_tiles;
-      const cudaError_t e = L.batch_step(s->d_lats, nres, t, ni, t + ni, ne, t + ni + ne, nl, (int)it, s->d_err,
-                                         s->stream, &s->fork);
+      const cudaError_t e = L.batch_step(shape, s->d_lats, nres, t, ni, t + ni, ne, t + ni + ne, nl, (int)it,
+                                         s->d_err, s->stream, &s->fork);
       if (e != cudaSuccess) return e;
     }
     return lbs::launch_batch_advance(s->d_lats, nres, (int)n, s->stream);
@@ -237,6 +237,19 @@ void run(lbs_server *s) {
   std::vector<BatchTile> ht;
   int ni = 0, ne = 0, nl = 0;  // interior tiles, frame tiles, frame tiles of two-point-extrapolation lattices
   bool dirty = true;
+  // Batch tile shape: fixed by the configuration, or picked by timing.  A
+  // trial runs one chunk on each shape (every shape computes each node with
+  // the same operations, so the results do not depend on it) and keeps the
+  // one with the most node updates per second of device time; a new trial
+  // starts when the resident node count has moved by a quarter since the last.
+  const bool tune = s->cfg.batch_shape == 0;
+  int shape = tune ? 0 : s->cfg.batch_shape - 1;
+  int trial = -1;            // shape under trial, -1 outside a trial
+  int64_t tuned_nodes = -1;  // resident nodes when the last trial ended
+  std::vector<double> rate;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
   const lbs::Launchers &L = s->cfg.precision == LBS_FP64   ? lbs::launchers_fp64()
                             : s->cfg.precision == LBS_FP32 ? lbs::launchers_fp32()
                                                            : lbs::launchers_fp16();
@@ -313,13 +326,22 @@ void run(lbs_server *s) {
       dirty = true;
     }
     if (res.empty()) continue;
+    int64_t nodes = 0;
+    for (Req *r : res) nodes += (int64_t)r->lat.nx * r->lat.ny;
+    if (tune && trial < 0 && (tuned_nodes < 0 || 4 * std::llabs(nodes - tuned_nodes) > tuned_nodes)) {
+      trial = 0;
+      rate.assign(L.nbatch_shapes, 0.0);
+      if (shape != 0) dirty = true;
+      shape = 0;
+    }
     // batch tables
     if (dirty) {
       graph.drop();
       hl.resize(res.size());
       ht.clear();
       std::vector<BatchTile> edge, edge_lin;
-      const int TX = L.batch_tile.tx, TY = L.batch_tile.ty;
+      const lbs::TileShape bs = L.batch_shape(shape);
+      const int TX = bs.tx, TY = bs.ty;
       for (size_t i = 0; i < res.size(); ++i) {
         lbs_handle *h = res[i]->h;
         BatchLattice &B = hl[i];
@@ -361,13 +383,35 @@ void run(lbs_server *s) {
     chunk = std::min(chunk, longest);
     const double tb = s->now();
     const int64_t launched = chunk * ((ni > 0) + (ne > 0) + (nl > 0)) + 1;
-    cudaError_t e = run_chunk(s, L, (int)res.size(), ni, ne, nl, chunk, graph);
+    int64_t work = 0;  // node updates this chunk executes
+    for (Req *r : res) work += (int64_t)r->lat.nx * r->lat.ny * std::min(chunk, r->nsteps - r->k);
+    if (trial >= 0) cudaEventRecord(ev0, s->stream);
+    cudaError_t e = run_chunk(s, L, shape, (int)res.size(), ni, ne, nl, chunk, graph);
+    if (trial >= 0) cudaEventRecord(ev1, s->stream);
     const cudaError_t es = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = es;
+    if (trial >= 0 && e == cudaSuccess) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      rate[trial] = ms > 0 ? (double)work / ms : 0.0;
+      if (++trial < L.nbatch_shapes) {
+        shape = trial;
+      } else {
+        shape = (int)(std::max_element(rate.begin(), rate.end()) - rate.begin());
+        trial = -1;
+        tuned_nodes = nodes;
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->st.batch_tunings += 1;
+      }
+      dirty = true;
+    }
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->st.busy_seconds += s->now() - tb;
       s->st.launches += launched;
+      s->st.batch_shape = shape;
+      s->st.batch_tx = L.batch_shape(shape).tx;
+      s->st.batch_ty = L.batch_shape(shape).ty;
       for (Req *r : res) r->k = std::min(r->k + chunk, r->nsteps);
     }
     // retire finished lattices, and every kCheckEvery iterations those that
@@ -387,6 +431,8 @@ void run(lbs_server *s) {
   }
   // shutdown: release what is still resident
   graph.drop();
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
   for (Req *r : res) {
     if (r->h) lbs_destroy(r->h);
     r->h = nullptr;
@@ -399,7 +445,11 @@ extern "C" {
 
 int lbs_server_create(const lbs_server_config *cfg, lbs_server **out) {
   if (!cfg || !out || cfg->precision < LBS_FP64 || cfg->precision > LBS_FP16S || cfg->chunk < 0 ||
-      cfg->max_resident < 0 || cfg->queue_limit < 0 || !(cfg->preempt_after_s >= 0)) {
+      cfg->max_resident < 0 || cfg->queue_limit < 0 || !(cfg->preempt_after_s >= 0) || cfg->batch_shape < 0 ||
+      cfg->batch_shape > (cfg->precision == LBS_FP64   ? lbs::launchers_fp64()
+                          : cfg->precision == LBS_FP32 ? lbs::launchers_fp32()
+                                                       : lbs::launchers_fp16())
+                             .nbatch_shapes) {
     lbs::set_error("bad server configuration");
     return LBS_EINVAL;
   }

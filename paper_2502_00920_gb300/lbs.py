@@ -81,6 +81,8 @@ SIGNATURES = {
     "lbs_fields_static": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
     "lbs_probe": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _dp]),
     "lbs_monitor": (ctypes.c_int, [_vp, ctypes.POINTER(Monitors)]),
+    "lbs_grid_error": (ctypes.c_int, [_vp, _dp, _dp]),
+    "lbs_grid_error_device": (ctypes.c_int, [_vp, ctypes.c_void_p, _dp]),
     "lbs_set_monitor_interval": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "lbs_set_graph_chunk": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "lbs_set_variant": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -115,7 +117,7 @@ SIGNATURES = {
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("precision", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("max_resident", ctypes.c_int32), ("queue_limit", ctypes.c_int32),
-                ("preempt_after_s", ctypes.c_double)]
+                ("preempt_after_s", ctypes.c_double), ("batch_shape", ctypes.c_int32)]
 
 
 class TicketInfo(ctypes.Structure):
@@ -129,7 +131,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("node_updates", ctypes.c_int64),
                 ("busy_seconds", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t),
-                ("launches", ctypes.c_int64), ("preemptions", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("preemptions", ctypes.c_int64), ("batch_shape", ctypes.c_int32),
+                ("batch_tx", ctypes.c_int32), ("batch_ty", ctypes.c_int32), ("batch_tunings", ctypes.c_int64)]
 
 
 # include/lbs_serve.h
@@ -393,6 +396,17 @@ class Simulation:
         check(lib().lbs_probe(self._h, int(idx.size), idx.ctypes.data_as(_i32p), _ptr(out)))
         return out
 
+    def grid_error(self, u_ref) -> tuple:
+        """(E2, Einf) of the current u against u_ref (Eq. griderror): a host
+        array [ny, nx, 2] or a device tensor of that shape (float64)."""
+        out = np.empty(2)
+        if hasattr(u_ref, "data_ptr"):
+            check(lib().lbs_grid_error_device(self._h, _dev_ptr(u_ref), _ptr(out)))
+        else:
+            a = np.ascontiguousarray(u_ref, dtype=np.float64)
+            check(lib().lbs_grid_error(self._h, _ptr(a), _ptr(out)))
+        return float(out[0]), float(out[1])
+
     def monitor(self) -> dict:
         m = Monitors()
         check(lib().lbs_monitor(self._h, ctypes.byref(m)))
@@ -427,9 +441,11 @@ class Server:
     """Continuous-batching server (include/lbs_serve.h)."""
 
     def __init__(self, precision: str = "fp32", hbm_budget: int = 0, chunk: int = 64, max_resident: int = 0,
-                 queue_limit: int = 0, preempt_after_s: float = 0.0):
+                 queue_limit: int = 0, preempt_after_s: float = 0.0, batch_shape: int | None = None):
+        """batch_shape: None lets the server time its batch tile shapes and
+        pick one; 0..3 fixes one."""
         cfg = ServerConfig(int(hbm_budget), PRECISION[precision], int(chunk), int(max_resident), int(queue_limit),
-                           float(preempt_after_s))
+                           float(preempt_after_s), 0 if batch_shape is None else int(batch_shape) + 1)
         h = _vp()
         check(lib().lbs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

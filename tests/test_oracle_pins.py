@@ -573,3 +573,20 @@ def test_linear_wall_value_is_the_field_at_the_wall(oracle_mod, xwall, ywall):
         assert other != at_wall
     # a node that is not on the named wall is refused
     assert np.isnan(oracle_mod.wall_value(case, a, 2, 2, "left", None))
+
+
+def test_grid_error_norms_worked_example(oracle_mod):
+    """Eq. griderror on two nodes, values checked by hand: u_ref = ((3, 4),
+    (0, 0)), du = ((0, 1), (-2, 0)); ||u_ref||_2 = 5, ||du||_2 = sqrt(5),
+    ||du||_inf = 2 (the larger |component| over nodes).  E2 = (1/n) sqrt(5)/5
+    with n = 2, Einf = 2/5.  A dropped 1/n, the computed field's norm in the
+    denominator or a maximum without absolute values each miss these."""
+    u_ref = np.array([[3.0, 4.0], [0.0, 0.0]])
+    u = u_ref + np.array([[0.0, 1.0], [-2.0, 0.0]])
+    e2, einf = oracle_mod.grid_error(u, u_ref)
+    assert abs(e2 - np.sqrt(5.0) / 10.0) <= 1e-16
+    assert einf == 0.4
+    # identical fields: no error; a field equal to twice the reference: du = u_ref
+    assert oracle_mod.grid_error(u_ref, u_ref) == (0.0, 0.0)
+    e2, einf = oracle_mod.grid_error(2 * u_ref, u_ref)
+    assert abs(e2 - 0.5) <= 1e-16 and einf == 4.0 / 5.0

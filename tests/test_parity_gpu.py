@@ -193,6 +193,24 @@ def test_fused_iterations_equal_single_ones_bitwise(L, oracle_mod, steps, chunk)
     assert rel(b[0], ur) <= TOL["fp32"]
 
 
+def test_grid_error_norms_match_the_oracle(L, oracle_mod):
+    """lbs_grid_error (host and device reference) against the oracle's
+    Eq. griderror on the same fields: the norms of the GPU's u against a
+    seeded reference."""
+    import torch
+    case = I.tension(70, 45, 0, ramp=50, model="nh", precision="fp32")
+    ref, _ = I.random_state(case.nx, case.ny, 11, amp_u=2e-3)
+    with L.Simulation(case) as s:
+        s.step(120)
+        s.sync()
+        u = s.fields(True, False, False)[0]
+        host = s.grid_error(ref)
+        dev = s.grid_error(torch.as_tensor(ref, device="cuda"))
+    want = oracle_mod.grid_error(u, ref)
+    for got in (host, dev):
+        assert abs(got[0] - want[0]) <= 1e-13 * want[0] and abs(got[1] - want[1]) <= 1e-13 * want[1], (got, want)
+
+
 def test_monitor_matches_oracle(L, oracle_mod):
     """max|u| and the total momentum (sum of the first moment of the stored
     post-collision populations = rho0 sum v on a periodic lattice without body

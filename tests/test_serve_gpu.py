@@ -210,3 +210,28 @@ def test_zero_iteration_requests_and_steps(L):
             u, v, P, rc = srv.result(tickets[0])
             assert rc == L.OK and all(srv.result(t)[3] == L.OK for t in tickets[1:])
         assert np.array_equal(u, ref[0]) and np.array_equal(v, ref[1]) and np.array_equal(P, ref[2])
+
+
+def test_batch_tile_shapes_give_the_same_results_and_are_tuned(L):
+    """The server's four batch tile shapes compute every node with the same
+    operations: fixing any of them, or letting the server time them and
+    switch mid-run, gives bitwise the same results (equal to the lattices run
+    alone); an unknown shape is refused."""
+    cases = mix("fp32")
+    ref = [alone(L, c) for c in cases]
+    for shape in (0, 1, 2, 3, None):
+        with L.Server(precision="fp32", chunk=16, batch_shape=shape) as srv:
+            tickets = [srv.submit(c) for c in cases]
+            srv.drain(120)
+            st = srv.stats()
+            results = [srv.result(t) for t in tickets]
+        if shape is None:
+            assert st["batch_tunings"] >= 1
+        else:
+            assert st["batch_shape"] == shape
+        for c, (u, v, P, rc), (ua, va, Pa) in zip(cases, results, ref):
+            assert rc == L.OK
+            assert np.array_equal(u, ua) and np.array_equal(v, va) and np.array_equal(P, Pa), (c.name, shape)
+    with pytest.raises(L.LbsError) as e:
+        L.Server(precision="fp32", batch_shape=7)
+    assert e.value.code == L.EINVAL
