@@ -357,6 +357,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16s"])
+    ap.add_argument("--variant", type=int, default=None, help="tile variant of the timed lattice (default: the "
+                    "precision's default variant)")
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--ref-n", type=int, default=1024)
@@ -393,7 +395,7 @@ def main():
     case = I.roofline(n=n, nsteps=args.e2e_steps, precision=args.precision, seed=5 + rank)
     stream = torch.cuda.Stream(device=dev)
     v0 = I.grf_velocity(case, device=dev)
-    sim = L.Simulation(case, stream=stream)
+    sim = L.Simulation(case, stream=stream, variant=args.variant)
     sim.set_initial(None, v0)
     sim.step(W)
     sim.sync()
@@ -421,6 +423,8 @@ def main():
     # average duration in the timed region (events on the launching stream)
     peak, peak_kind = peaks()
     bpn = BYTES_PER_NODE[args.precision]
+    if L.tile_variant_name(args.precision, variant) == "step_fused2_tma_kernel":
+        bpn = bpn / 2  # two iterations per pass over the state (periodic lattice)
     achieved = bpn * cells / (ms / K * 1e-3) / 1e9
     traffic = profile_traffic(args.precision, n)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -444,7 +448,7 @@ def main():
         torch.cuda.empty_cache()
         uo = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
         vo = torch.empty((n, n, 2), dtype=torch.float64, pin_memory=True)
-        sim = L.Simulation(case, stream=stream)
+        sim = L.Simulation(case, stream=stream, variant=args.variant)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -92,16 +92,17 @@ __device__ __forceinline__ void udiff(const float4 &a, const float4 &b, float &d
 
 __device__ __forceinline__ double2 uadd(const double2 &u, double dx, double dy) { return make_double2(u.x + dx, u.y + dy); }
 
-// compensated accumulation: (hi, lo) + d with the rounding error of hi + d
-// (two-sum, Knuth) folded into lo, then renormalised (fast two-sum)
+// compensated accumulation: (hi, lo) + d.  hi takes the rounded sum; the
+// rounding error of hi + d (two-sum, Knuth: exact) is added to lo, which so
+// gathers the errors of all increments; the value is hi + lo.  (lo is not
+// renormalised into hi: it stays a small multiple of hi's rounding unit, far
+// inside its own range, and the finite differences take both parts.)
 __device__ __forceinline__ void pair_add(float &hi, float &lo, float d) {
-  float s = hi + d;
-  float bp = s - hi;
-  float e = (hi - (s - bp)) + (d - bp);
-  float l = lo + e;
-  float h2 = s + l;
-  lo = l - (h2 - s);
-  hi = h2;
+  const float s = hi + d;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (d - bp);
+  lo = lo + e;
+  hi = s;
 }
 __device__ __forceinline__ float4 uadd(const float4 &u, float dx, float dy) {
   float4 r = u;
