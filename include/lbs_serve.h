@@ -33,10 +33,12 @@
  * Batch tile shapes (no counterpart in the paper).  The batched kernels come
  * in the four global-memory tile shapes of lbs_tile_variants (0..3), which
  * compute every node with the same operations.  Unless batch_shape fixes
- * one, the worker times them: a trial runs one chunk on each shape (real
- * work, not a rehearsal) and keeps the one with the most node updates per
- * second of device time; a new trial starts when the resident node count has
- * moved by a quarter since the last.  Results do not depend on the shape.
+ * one, the worker times them: a trial runs one chunk on each candidate
+ * shape (real work, not a rehearsal) and keeps the one with the most node
+ * updates per second of device time.  The first trial takes all four; a new
+ * trial starts when the resident node count has halved or doubled since the
+ * last, and takes the two fastest of the previous one.  Results do not
+ * depend on the shape.
  *
  * The server owns its device memory and its results until lbs_result hands
  * them over.  All functions are thread-safe.

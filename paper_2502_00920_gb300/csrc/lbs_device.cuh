@@ -445,7 +445,10 @@ __device__ __forceinline__ void gather(const Params &P, const typename Pr::gs *_
   const size_t plane = (size_t)P.ny * P.pitch;
   const size_t idx = (size_t)y * P.pitch + x;
   R g0[9];
-  if (!EDGE) {
+  // every streaming source inside the lattice without wrapping: loads at
+  // fixed offsets, no boundary rule (all interior tiles, and most nodes of
+  // the frame tiles, which lie within three nodes of a wall or of the end)
+  if (!EDGE || (x >= 1 && x <= P.nx - 2 && y >= 1 && y <= P.ny - 2)) {
 #pragma unroll
     for (int q = 0; q < 9; ++q) f[q] = gload(g, q * plane + idx - ex(q) - (ptrdiff_t)ey(q) * P.pitch, inv);
 #pragma unroll

@@ -238,15 +238,18 @@ void run(lbs_server *s) {
   int ni = 0, ne = 0, nl = 0;  // interior tiles, frame tiles, frame tiles of two-point-extrapolation lattices
   bool dirty = true;
   // Batch tile shape: fixed by the configuration, or picked by timing.  A
-  // trial runs one chunk on each shape (every shape computes each node with
-  // the same operations, so the results do not depend on it) and keeps the
-  // one with the most node updates per second of device time; a new trial
-  // starts when the resident node count has moved by a quarter since the last.
+  // trial runs one chunk on each candidate shape (every shape computes each
+  // node with the same operations, so the results do not depend on it) and
+  // keeps the one with the most node updates per second of device time.  The
+  // first trial takes every shape; a new one starts when the resident node
+  // count has halved or doubled since the last, and takes the two fastest of
+  // the previous trial (a trial's chunks on slow shapes cost throughput).
   const bool tune = s->cfg.batch_shape == 0;
   int shape = tune ? 0 : s->cfg.batch_shape - 1;
-  int trial = -1;            // shape under trial, -1 outside a trial
+  int trial = -1;            // place in `cand` of the shape under trial, -1 outside a trial
   int64_t tuned_nodes = -1;  // resident nodes when the last trial ended
-  std::vector<double> rate;
+  std::vector<int> cand;     // shapes of the current trial
+  std::vector<double> rate;  // node updates per ms of each shape, last measured
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
@@ -328,11 +331,20 @@ void run(lbs_server *s) {
     if (res.empty()) continue;
     int64_t nodes = 0;
     for (Req *r : res) nodes += (int64_t)r->lat.nx * r->lat.ny;
-    if (tune && trial < 0 && (tuned_nodes < 0 || 4 * std::llabs(nodes - tuned_nodes) > tuned_nodes)) {
+    if (tune && trial < 0 && (tuned_nodes < 0 || nodes >= 2 * tuned_nodes || 2 * nodes <= tuned_nodes)) {
+      cand.clear();
+      if (tuned_nodes < 0) {
+        rate.assign(L.nbatch_shapes, 0.0);
+        for (int b = 0; b < L.nbatch_shapes; ++b) cand.push_back(b);
+      } else {
+        std::vector<int> order(L.nbatch_shapes);
+        for (int b = 0; b < L.nbatch_shapes; ++b) order[b] = b;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return rate[a] > rate[b]; });
+        cand.assign(order.begin(), order.begin() + std::min(2, L.nbatch_shapes));
+      }
       trial = 0;
-      rate.assign(L.nbatch_shapes, 0.0);
-      if (shape != 0) dirty = true;
-      shape = 0;
+      if (shape != cand[0]) dirty = true;
+      shape = cand[0];
     }
     // batch tables
     if (dirty) {
@@ -393,11 +405,13 @@ void run(lbs_server *s) {
     if (trial >= 0 && e == cudaSuccess) {
       float ms = 0;
       cudaEventElapsedTime(&ms, ev0, ev1);
-      rate[trial] = ms > 0 ? (double)work / ms : 0.0;
-      if (++trial < L.nbatch_shapes) {
-        shape = trial;
+      rate[shape] = ms > 0 ? (double)work / ms : 0.0;
+      if (++trial < (int)cand.size()) {
+        shape = cand[trial];
       } else {
-        shape = (int)(std::max_element(rate.begin(), rate.end()) - rate.begin());
+        shape = cand[0];
+        for (int b : cand)
+          if (rate[b] > rate[shape]) shape = b;
         trial = -1;
         tuned_nodes = nodes;
         std::lock_guard<std::mutex> lk(s->mu);
