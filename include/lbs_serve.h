@@ -13,6 +13,10 @@
  * its iteration count stops (its tiles return at once), is checked for
  * non-finite values, has u, v and P copied to host memory owned by the server
  * and its device memory released, after which queued requests are admitted.
+ * Host work overlaps the GPU's: the worker launches a chunk and, while it
+ * runs, creates the handles of newly admitted requests and finishes the
+ * lattices that left the batch after the previous chunk; it waits for the
+ * chunk only then.
  * Every 1000 iterations (at the next scheduling point) each resident lattice
  * is also checked for non-finite values; one that has some is retired at once
  * as LBS_EUNSTABLE, like a handle whose monitor saw them.

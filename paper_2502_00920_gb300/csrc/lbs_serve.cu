@@ -140,6 +140,11 @@ bool ensure(T *&ptr, int &cap, int need) {
 // interval as a handle's default monitor)
 constexpr int64_t kCheckEvery = 1000;
 
+// requests admitted at one scheduling point at most: a long queue joins the
+// batch over several chunks, its handles created while the GPU runs the
+// chunks of the lattices already admitted
+constexpr int kAdmitPerChunk = 16;
+
 // bring the handle up to date with the batch's advance of the lattice
 void sync_handle(Req *r) {
   lbs_handle *h = r->h;
@@ -232,7 +237,8 @@ void run(lbs_server *s) {
   cudaSetDevice(s->device);
   int64_t since_check = 0;
   ChunkGraph graph;
-  std::vector<Req *> res;
+  std::vector<Req *> res;                     // lattices in the batch tables
+  std::vector<std::pair<Req *, int>> retire;  // left the batch; finished while the next chunk runs
   std::vector<BatchLattice> hl;
   std::vector<BatchTile> ht;
   int ni = 0, ne = 0, nl = 0;  // interior tiles, frame tiles, frame tiles of two-point-extrapolation lattices
@@ -256,12 +262,76 @@ void run(lbs_server *s) {
   const lbs::Launchers &L = s->cfg.precision == LBS_FP64   ? lbs::launchers_fp64()
                             : s->cfg.precision == LBS_FP32 ? lbs::launchers_fp32()
                                                            : lbs::launchers_fp16();
+  // The chunk in flight.  The worker launches a chunk and, while the GPU runs
+  // it, creates the handles of newly admitted requests and finishes the
+  // lattices that left the batch after the previous chunk (their fields
+  // copied out, their memory released); only then does it wait for the chunk.
+  struct Flight {
+    bool on = false;
+    cudaError_t err = cudaSuccess;
+    int64_t chunk = 0, work = 0, launched = 0, nodes = 0;
+    int shape = 0;
+    bool timed = false;
+    double t0 = 0;
+  } fl;
+  // wait for the chunk in flight, account for it, and move the lattices that
+  // reached their end (and, every kCheckEvery iterations, those that went
+  // non-finite) from the batch to `retire`
+  auto complete = [&]() {
+    if (!fl.on) return;
+    fl.on = false;
+    cudaError_t e = fl.err;
+    const cudaError_t es = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = es;
+    if (fl.timed && e == cudaSuccess) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      rate[fl.shape] = ms > 0 ? (double)fl.work / ms : 0.0;
+      if (++trial < (int)cand.size()) {
+        shape = cand[trial];
+      } else {
+        shape = cand[0];
+        for (int b : cand)
+          if (rate[b] > rate[shape]) shape = b;
+        trial = -1;
+        tuned_nodes = fl.nodes;
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->st.batch_tunings += 1;
+      }
+      dirty = true;
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->st.busy_seconds += s->now() - fl.t0;
+      s->st.launches += fl.launched;
+      s->st.batch_shape = fl.shape;
+      s->st.batch_tx = L.batch_shape(fl.shape).tx;
+      s->st.batch_ty = L.batch_shape(fl.shape).ty;
+      for (Req *r : res) r->k = std::min(r->k + fl.chunk, r->nsteps);
+    }
+    since_check += fl.chunk;
+    const bool check = since_check >= kCheckEvery;
+    if (check) since_check = 0;
+    std::vector<Req *> keep;
+    for (Req *r : res) {
+      if (e != cudaSuccess) retire.emplace_back(r, LBS_ECUDA);
+      else if (r->k >= r->nsteps) retire.emplace_back(r, LBS_OK);
+      else if (check && unstable(r)) retire.emplace_back(r, LBS_EUNSTABLE);
+      else keep.push_back(r);
+    }
+    if (keep.size() != res.size()) dirty = true;
+    res.swap(keep);
+  };
+  auto finish_retired = [&]() {
+    for (auto &x : retire) finish(s, x.first, x.second);
+    retire.clear();
+  };
   for (;;) {
     // admission: FIFO while the footprint fits
     std::vector<Req *> admit, victims;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      if (res.empty() && s->queue.empty()) {
+      if (res.empty() && s->queue.empty() && !fl.on && retire.empty()) {
         if (s->stop) break;
         s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
         if (s->stop && s->queue.empty()) break;
@@ -270,7 +340,7 @@ void run(lbs_server *s) {
       while (!s->queue.empty()) {
         Req *r = s->queue.front();
         if (s->cfg.max_resident > 0 && (int)(res.size() + admit.size()) >= s->cfg.max_resident) break;
-        if (s->used + r->bytes > s->cfg.hbm_budget) break;
+        if (s->used + r->bytes > s->cfg.hbm_budget || (int)admit.size() >= kAdmitPerChunk) break;
         s->queue.pop_front();
         s->used += r->bytes;
         s->st.queued -= 1;
@@ -284,8 +354,14 @@ void run(lbs_server *s) {
         victims = pick_victims(s, res, s->queue.front(), now, s->cfg.preempt_after_s);
     }
     // swap the victims out: state to host memory, device memory released; they
-    // rejoin the queue at the back and resume from their saved state
+    // rejoin the queue at the back and resume from their saved state (the
+    // chunk in flight is waited for first: it advances their state)
+    if (!victims.empty()) {
+      complete();
+      finish_retired();
+    }
     for (Req *r : victims) {
+      if (std::find(res.begin(), res.end(), r) == res.end()) continue;  // it finished meanwhile
       sync_handle(r);
       r->ckpt.resize(lbs_checkpoint_bytes(r->h));
       const int rc = lbs_save(r->h, r->ckpt.data(), r->ckpt.size());
@@ -309,6 +385,9 @@ void run(lbs_server *s) {
       dirty = true;
     }
     if (!victims.empty()) continue;  // admit into the room just made
+    // new handles (their initialisation runs on their own streams, beside the
+    // chunk in flight)
+    std::vector<Req *> created;
     for (Req *r : admit) {
       int rc = lbs_create(&r->lat, &r->mat, &r->bcs, &r->h);
       if (!rc && !r->ckpt.empty()) rc = lbs_load(r->h, r->ckpt.data(), r->ckpt.size());
@@ -325,10 +404,15 @@ void run(lbs_server *s) {
       r->state = LBS_TICKET_RUNNING;
       if (r->t_admit < 0) r->t_admit = s->now();
       r->t_resident = s->now();
-      res.push_back(r);
-      dirty = true;
+      created.push_back(r);
     }
-    if (res.empty()) continue;
+    complete();
+    for (Req *r : created) res.push_back(r);
+    if (!created.empty()) dirty = true;
+    if (res.empty()) {
+      finish_retired();
+      continue;
+    }
     int64_t nodes = 0;
     for (Req *r : res) nodes += (int64_t)r->lat.nx * r->lat.ny;
     if (tune && trial < 0 && (tuned_nodes < 0 || nodes >= 2 * tuned_nodes || 2 * nodes <= tuned_nodes)) {
@@ -380,70 +464,38 @@ void run(lbs_server *s) {
       ht.insert(ht.end(), edge.begin(), edge.end());
       ht.insert(ht.end(), edge_lin.begin(), edge_lin.end());
       if (!ensure(s->d_lats, s->lat_cap, (int)hl.size()) || !ensure(s->d_tiles, s->tile_cap, (int)ht.size())) {
-        for (Req *r : res) finish(s, r, LBS_ENOMEM);
+        for (Req *r : res) retire.emplace_back(r, LBS_ENOMEM);
         res.clear();
+        finish_retired();
         continue;
       }
       cudaMemcpyAsync(s->d_lats, hl.data(), sizeof(BatchLattice) * hl.size(), cudaMemcpyHostToDevice, s->stream);
       cudaMemcpyAsync(s->d_tiles, ht.data(), sizeof(BatchTile) * ht.size(), cudaMemcpyHostToDevice, s->stream);
       dirty = false;
     }
-    // one chunk of iterations for every resident lattice
+    // one chunk of iterations for every resident lattice, launched; the
+    // lattices that left the batch are finished while it runs
     int64_t chunk = s->cfg.chunk;
     int64_t longest = 0;
     for (Req *r : res) longest = std::max(longest, r->nsteps - r->k);
     chunk = std::min(chunk, longest);
-    const double tb = s->now();
-    const int64_t launched = chunk * ((ni > 0) + (ne > 0) + (nl > 0)) + 1;
-    int64_t work = 0;  // node updates this chunk executes
-    for (Req *r : res) work += (int64_t)r->lat.nx * r->lat.ny * std::min(chunk, r->nsteps - r->k);
-    if (trial >= 0) cudaEventRecord(ev0, s->stream);
-    cudaError_t e = run_chunk(s, L, shape, (int)res.size(), ni, ne, nl, chunk, graph);
-    if (trial >= 0) cudaEventRecord(ev1, s->stream);
-    const cudaError_t es = cudaStreamSynchronize(s->stream);
-    if (e == cudaSuccess) e = es;
-    if (trial >= 0 && e == cudaSuccess) {
-      float ms = 0;
-      cudaEventElapsedTime(&ms, ev0, ev1);
-      rate[shape] = ms > 0 ? (double)work / ms : 0.0;
-      if (++trial < (int)cand.size()) {
-        shape = cand[trial];
-      } else {
-        shape = cand[0];
-        for (int b : cand)
-          if (rate[b] > rate[shape]) shape = b;
-        trial = -1;
-        tuned_nodes = nodes;
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->st.batch_tunings += 1;
-      }
-      dirty = true;
-    }
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->st.busy_seconds += s->now() - tb;
-      s->st.launches += launched;
-      s->st.batch_shape = shape;
-      s->st.batch_tx = L.batch_shape(shape).tx;
-      s->st.batch_ty = L.batch_shape(shape).ty;
-      for (Req *r : res) r->k = std::min(r->k + chunk, r->nsteps);
-    }
-    // retire finished lattices, and every kCheckEvery iterations those that
-    // went non-finite
-    since_check += chunk;
-    const bool check = since_check >= kCheckEvery;
-    if (check) since_check = 0;
-    std::vector<Req *> keep;
-    for (Req *r : res) {
-      if (e != cudaSuccess) finish(s, r, LBS_ECUDA);
-      else if (r->k >= r->nsteps) finish(s, r, LBS_OK);
-      else if (check && unstable(r)) finish(s, r, LBS_EUNSTABLE);
-      else keep.push_back(r);
-    }
-    if (keep.size() != res.size()) dirty = true;
-    res.swap(keep);
+    fl.t0 = s->now();
+    fl.chunk = chunk;
+    fl.launched = chunk > 0 ? chunk * ((ni > 0) + (ne > 0) + (nl > 0)) + 1 : 0;
+    fl.work = 0;  // node updates this chunk executes
+    for (Req *r : res) fl.work += (int64_t)r->lat.nx * r->lat.ny * std::min(chunk, r->nsteps - r->k);
+    fl.nodes = nodes;
+    fl.shape = shape;
+    fl.timed = trial >= 0;
+    if (fl.timed) cudaEventRecord(ev0, s->stream);
+    fl.err = run_chunk(s, L, shape, (int)res.size(), ni, ne, nl, chunk, graph);
+    if (fl.timed) cudaEventRecord(ev1, s->stream);
+    fl.on = true;
+    finish_retired();
   }
-  // shutdown: release what is still resident
+  // shutdown: wait for the chunk in flight, release what is still resident
+  complete();
+  finish_retired();
   graph.drop();
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
