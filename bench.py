@@ -186,7 +186,7 @@ def run_reference(args, rank: int, world: int):
 def fp64_alu_roofline(mlups: float):
     """FP64 is bound by the FP64 pipe, not HBM: FLOP per node from the
     committed ncu record (if taken on the current kernel source) against the
-    measured FP64 FMA throughput; else None."""
+    FP64 FMA rate of the GPU (2 per clock per SM); else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "step_fp64_alu.json")) as f:
             rec = json.load(f)
@@ -196,7 +196,7 @@ def fp64_alu_roofline(mlups: float):
         achieved = rec["flops_per_node"] * mlups * 1e6 / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": rec["peak_tflops"], "unit": "TFLOP/s",
                 "frac": achieved / rec["peak_tflops"], "flops_per_node": rec["flops_per_node"],
-                "fp64_pipe_active_ncu": rec["fp64_pipe_active"], "peak_source": "measured FP64 FMA probe"}
+                "fp64_pipe_active_ncu": rec["fp64_pipe_active"], "peak_source": rec["peak_source"]}
     except Exception:
         return None
 

@@ -38,7 +38,7 @@ def _sources():
         os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
 
 
-STEP_KERNEL_SOURCES = ["lbs_device.cuh", "lbs_internal.h", "kernels_fp64.cu", "kernels_fp32.cu", "kernels_fp16.cu"]
+STEP_KERNEL_SOURCES = ["lbs_device.cuh", "lbs_tiles.h", "lbs_internal.h", "kernels_fp64.cu", "kernels_fp32.cu", "kernels_fp16.cu"]
 
 
 def source_hash() -> str:
