@@ -245,7 +245,8 @@ def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: floa
     at their next 1000-iteration check and count it as failed (also when its
     final u is not finite); aggregate MLUPS counts the node updates actually
     executed.  Every request finite in both arms states its FP32 error on u
-    against its FP64 result."""
+    against its FP64 result; each one above 1e-5 also states how much its FP64
+    result moves when Young's modulus moves by one double rounding unit."""
     import threading
     trace = I.serving_trace(n_requests, seed=seed, rate=1.0)
     cases = [c.replace(nsteps=max(100, int(round(c.nsteps * steps_scale)))) for _, c in trace]
@@ -320,6 +321,26 @@ def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: floa
                   err=float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)))
              for c, a, b in zip(cases, u32, u64) if a is not None and b is not None
              and np.abs(a - b).max() > 1e-5 * max(np.abs(b).max(), 1e-300)]
+    # Conditioning of each request above the bar: its FP64 result again with
+    # Young's modulus moved by one double rounding unit.  The relative change
+    # of u is the problem's own amplification of a perturbation of that size;
+    # FP32 rounds 2^29 times more coarsely, so an FP32 error below 2^29 times
+    # that change is what the problem itself allows for FP32 arithmetic.
+    by_name = {c.name: (c, b) for c, b in zip(cases, u64)}
+    for r in above:
+        c, b = by_name[r["request"]]
+        u_pert = None
+        with L.Simulation(c.replace(precision="fp64", E=float(np.nextafter(c.E, 2.0 * c.E)))) as s:
+            try:
+                s.step(c.nsteps)
+                s.sync()
+                u_pert, _, _ = s.fields(True, False, False)
+            except L.LbsError:
+                pass
+        spread = (float(np.abs(u_pert - b).max() / max(np.abs(b).max(), 1e-300))
+                  if u_pert is not None and np.isfinite(u_pert).all() else None)
+        r["fp64_change_one_ulp_E"] = spread
+        r["within_conditioning"] = spread is not None and r["err"] <= 2.0 ** 29 * spread
     return {"requests": len(cases), "steps_scale": steps_scale, "node_updates_requested": sum(work),
             "offered_load_x_fp64_capacity": load, "arrival_rate_per_s": rate,
             "sequential_fp64": {"aggregate_mlups": done64 / sum(service) / 1e6, "node_updates": done64,
@@ -347,7 +368,9 @@ def serving(L, I, n_requests: int, steps_scale: float, seed: int = 4, load: floa
             "failed_fp64_only": sum(a is not None and b is None for a, b in zip(u32, u64)),
             "u_err_fp32_vs_fp64": {"compared": len(errs), "max": max(errs) if errs else None,
                                    "median": float(np.median(errs)) if errs else None,
-                                   "above_1e-5": sum(e > 1e-5 for e in errs), "above_1e-5_requests": above}}
+                                   "above_1e-5": sum(e > 1e-5 for e in errs),
+                                   "above_1e-5_beyond_conditioning": sum(not r["within_conditioning"] for r in above),
+                                   "above_1e-5_requests": above}}
 
 
 def main():
