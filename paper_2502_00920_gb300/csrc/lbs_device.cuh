@@ -774,10 +774,9 @@ cudaError_t launch_step(const Params &P, const StepPtrs &S, cudaStream_t st) {
 // the start of the chunk, it: this launch's place in the chunk).
 // SPLIT (frame tiles only): each table tile is run as CPT tiles of one node
 // per thread.
-template <class C, bool EDGE, bool LIN = false, bool SPLIT = false>
-__global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) batch_step_kernel(const BatchLattice *lats,
-                                                                                  const BatchTile *tiles, int ntiles,
-                                                                                  int it, int *err) {
+template <class C, bool EDGE, bool LIN, bool SPLIT>
+__device__ __forceinline__ void batch_walk(const BatchLattice *lats, const BatchTile *tiles, int ntiles, int it,
+                                           int *err) {
   using H = typename FrameCfg<C, SPLIT>::type;
   constexpr int parts = C::TY / H::TY;
   __shared__ Params sP;
@@ -811,6 +810,23 @@ __global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) batch_step_kerne
     }
     __syncthreads();  // the next tile reuses the shared memory
   }
+}
+
+template <class C, bool EDGE, bool LIN = false, bool SPLIT = false>
+__global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) batch_step_kernel(const BatchLattice *lats,
+                                                                                  const BatchTile *tiles, int ntiles,
+                                                                                  int it, int *err) {
+  batch_walk<C, EDGE, LIN, SPLIT>(lats, tiles, ntiles, it, err);
+}
+
+// The same walk over frame tiles (own wall values), held to three blocks per
+// SM: a frame tile waits on the latency of its global loads, and a third
+// block per SM hides more of it than the registers it gives up cost (single
+// precision; the FP16-storage and FP64 frame code would spill)
+template <class C>
+__global__ void __launch_bounds__(C::NT, 3) batch_frame3_kernel(const BatchLattice *lats, const BatchTile *tiles,
+                                                                int ntiles, int it, int *err) {
+  batch_walk<C, true, false, false>(lats, tiles, ntiles, it, err);
 }
 
 // launch `it` of a chunk: the interior tiles and the frame tiles of every
@@ -852,7 +868,12 @@ cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *in
         return;
       }
     }
-    if (ne > 0) batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, it, err);
+    if (ne > 0) {
+      if constexpr (sizeof(typename C::gs) == 4 && sizeof(typename C::real) == 4)
+        batch_frame3_kernel<C><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, it, err);
+      else
+        batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, it, err);
+    }
     if (nl > 0)
       batch_step_kernel<C, true, true><<<nl < blocks ? nl : blocks, C::NT, 0, fs>>>(lats, edge_lin, nl, it, err);
   };
