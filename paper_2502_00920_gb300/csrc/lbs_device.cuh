@@ -111,6 +111,15 @@ __device__ __forceinline__ float4 uadd(const float4 &u, float dx, float dy) {
   return r;
 }
 
+// u + kap * (mx, my): one rounding per component in double; the float pair
+// adds the rounded increment compensated
+__device__ __forceinline__ double2 uadd_k(const double2 &u, double kap, double mx, double my) {
+  return make_double2(fma(kap, mx, u.x), fma(kap, my, u.y));
+}
+__device__ __forceinline__ float4 uadd_k(const float4 &u, float kap, float mx, float my) {
+  return uadd(u, kap * mx, kap * my);
+}
+
 __device__ __forceinline__ double2 u_value(const double2 &u) { return u; }
 __device__ __forceinline__ double2 u_value(const float4 &u) {
   return make_double2((double)u.x + (double)u.z, (double)u.y + (double)u.w);
@@ -388,8 +397,24 @@ __device__ void wall_rules(const Params &P, const R *bnd, const G *g, const doub
 // the literal moment form, but every intermediate is of the size of the
 // populations, so single-precision rounding stays at the level of the stored
 // values instead of that of the second moments.
+// Per-thread constants of the collision: -omega, the relaxation of the even
+// part per unit Q for the axis (omega/18) and diagonal (-omega/36)
+// populations, and the forcing weights sigma/9 and sigma/36 times the storage
+// scale of g (the source arrives unscaled).
 template <class R>
-__device__ __forceinline__ void collide(R f[9], R Sx, R Sy, R omega, R sigma) {
+struct CollideK {
+  R mo, a1, a5, s9, s36;
+};
+template <class R>
+__device__ __forceinline__ CollideK<R> collide_k(R omega, R sigma, R scl) {
+  const R ss = sigma * scl;
+  return {-omega, omega * (R(1) / R(18)), -omega * (R(1) / R(36)), ss * (R(1) / R(9)), ss * (R(1) / R(36))};
+}
+
+// Each opposite pair takes the even relaxation A (same for both) and the odd
+// part b = -omega o + forcing with opposite signs: g = (f + A) +- b.
+template <class R>
+__device__ __forceinline__ void collide(R f[9], R Sx, R Sy, const CollideK<R> &K) {
   const R s13 = f[1] + f[3], s24 = f[2] + f[4], s57 = f[5] + f[7], s68 = f[6] + f[8];
   const R d13 = f[1] - f[3], d24 = f[2] - f[4], d57 = f[5] - f[7], d68 = f[6] - f[8];
   // (the products by 2 and 4 are exact)
@@ -399,20 +424,20 @@ __device__ __forceinline__ void collide(R f[9], R Sx, R Sy, R omega, R sigma) {
   const R oy = fmr(d24, c6, -((d57 + d68) * c3));
   const R o57 = fmr(d57, c3, -((d13 + d24) * c12));
   const R o68 = fmr(d68, c3, -((d24 - d13) * c12));
-  const R ne0 = Q * (R(1) / R(9)), ne1 = Q * (R(-1) / R(18)), ne5 = Q * (R(1) / R(36));
-  const R sx = sigma * Sx, sy = sigma * Sy;
-  const R fx = sx * (R(1) / R(9)), fy = sy * (R(1) / R(9));
-  const R f57 = (sx + sy) * (R(1) / R(36)), f68 = (sy - sx) * (R(1) / R(36));
-  const R mo = -omega;
-  f[0] = fmr(mo, ne0, f[0]);
-  f[1] = fmr(mo, ne1 + ox, f[1]) + fx;
-  f[3] = fmr(mo, ne1 - ox, f[3]) - fx;
-  f[2] = fmr(mo, ne1 + oy, f[2]) + fy;
-  f[4] = fmr(mo, ne1 - oy, f[4]) - fy;
-  f[5] = fmr(mo, ne5 + o57, f[5]) + f57;
-  f[7] = fmr(mo, ne5 - o57, f[7]) - f57;
-  f[6] = fmr(mo, ne5 + o68, f[6]) + f68;
-  f[8] = fmr(mo, ne5 - o68, f[8]) - f68;
+  const R fx = Sx * K.s9, fy = Sy * K.s9;
+  const R f57 = (Sx + Sy) * K.s36, f68 = (Sy - Sx) * K.s36;
+  const R A1 = Q * K.a1, A5 = Q * K.a5;
+  const R bx = fmr(K.mo, ox, fx), by = fmr(K.mo, oy, fy);
+  const R b57 = fmr(K.mo, o57, f57), b68 = fmr(K.mo, o68, f68);
+  f[0] = fmr(K.mo, Q * (R(1) / R(9)), f[0]);
+  f[1] = (f[1] + A1) + bx;
+  f[3] = (f[3] + A1) - bx;
+  f[2] = (f[2] + A1) + by;
+  f[4] = (f[4] + A1) - by;
+  f[5] = (f[5] + A5) + b57;
+  f[7] = (f[7] + A5) - b57;
+  f[6] = (f[6] + A5) + b68;
+  f[8] = (f[8] + A5) - b68;
 }
 
 // ------------------------------------------------------------------ tiles
@@ -545,15 +570,15 @@ struct Fd {
     H[2] = dxy * sx;
     H[3] = dyy * sy;
   }
-  // S = div N at R1 position (rx, ry) of a tile node
+  // S = div N + (sbx, sby) at R1 position (rx, ry) of a tile node
   static __device__ __forceinline__ void div(const typename C::Smem &sm, const Params &P, int rx, int ry, int gxn,
-                                             int gyn, R idx_, R &Sx, R &Sy) {
+                                             int gyn, R idx_, R sbx, R sby, R &Sx, R &Sy) {
     int xa, xb, ya, yb;
     bool onex, oney;
     fd_taps<EDGE>(P, rx, ry, gxn, gyn, xa, xb, ya, yb, onex, oney);
     const R sx = onex ? idx_ : R(0.5) * idx_, sy = oney ? idx_ : R(0.5) * idx_;
-    Sx = fmr(sm.n[0][ry][xa] - sm.n[0][ry][xb], sx, (sm.n[1][ya][rx] - sm.n[1][yb][rx]) * sy);
-    Sy = fmr(sm.n[2][ry][xa] - sm.n[2][ry][xb], sx, (sm.n[3][ya][rx] - sm.n[3][yb][rx]) * sy);
+    Sx = fmr(sm.n[0][ry][xa] - sm.n[0][ry][xb], sx, fmr(sm.n[1][ya][rx] - sm.n[1][yb][rx], sy, sbx));
+    Sy = fmr(sm.n[2][ry][xa] - sm.n[2][ry][xb], sx, fmr(sm.n[3][ya][rx] - sm.n[3][yb][rx], sy, sby));
   }
 };
 
@@ -620,7 +645,7 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     gather<typename C::PrT, EDGE, LIN>(P, g, bnd, sev, x, y, inv, f[i], gxm, gym, scl);
     R fx, fy;
     first_moment(f[i], fx, fy);
-    sm.u[ly + 2][lx + 2] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
+    sm.u[ly + 2][lx + 2] = uadd_k(u[(size_t)y * P.pitch + x], kap, gxm + fx, gym + fy);
   }
   // phase 1b: the 2-node frame (u only)
   for (int e = threadIdx.x; e < C::NRING; e += C::NT) {
@@ -632,14 +657,15 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     gather<typename C::PrT, EDGE, LIN>(P, g, bnd, sev, x, y, inv, ff, gxm, gym, scl);
     R fx, fy;
     first_moment(ff, fx, fy);
-    sm.u[ry][rx] = uadd(u[(size_t)y * P.pitch + x], kap * (gxm + fx), kap * (gym + fy));
+    sm.u[ry][rx] = uadd_k(u[(size_t)y * P.pitch + x], kap, gxm + fx, gym + fy);
   }
   __syncthreads();
   phase_n<C, EDGE, LIN>(sm, P, x0, y0, (R *)S.b_out);
   __syncthreads();
   // phase 3: source, collision, store
   const size_t plane = (size_t)P.ny * P.pitch;
-  const R omega = (R)P.omega, sigma = (R)P.sigma, idx_ = (R)P.inv_dx;
+  const R idx_ = (R)P.inv_dx;
+  const CollideK<R> K = collide_k<R>((R)P.omega, (R)P.sigma, scl);
   const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
 #pragma unroll
   for (int i = 0; i < C::CPT; ++i) {
@@ -647,10 +673,8 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
     const int x = x0 + lx, y = y0 + ly;
     if (EDGE && (x >= P.nx || y >= P.ny)) continue;
     R Sx, Sy;
-    Fd<C, EDGE>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
-    Sx += sbx;
-    Sy += sby;
-    collide<R>(f[i], Sx * scl, Sy * scl, omega, sigma);
+    Fd<C, EDGE>::div(sm, P, lx + 1, ly + 1, x, y, idx_, sbx, sby, Sx, Sy);
+    collide<R>(f[i], Sx, Sy, K);
     const size_t idx = (size_t)y * P.pitch + x;
 #pragma unroll
     for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[i][q], scl);
@@ -996,7 +1020,7 @@ __device__ __forceinline__ void tma_tile(const Params &P, const StepPtrs &S, con
     R gx, gy, fx, fy;
     first_moment(o, gx, gy);
     first_moment(p, fx, fy);
-    su[e] = uadd(su[e], kap * (gx + fx), kap * (gy + fy));
+    su[e] = uadd_k(su[e], kap, gx + fx, gy + fy);
   }
   __syncthreads();
   // phase 2: N on R1
@@ -1045,7 +1069,7 @@ __device__ __forceinline__ void tma_tile(const Params &P, const StepPtrs &S, con
   __syncthreads();
   // phase 3: stream again from shared memory, source, collision, store
   const size_t plane = (size_t)P.ny * P.pitch;
-  const R omega = (R)P.omega, sigma = (R)P.sigma;
+  const CollideK<R> K = collide_k<R>((R)P.omega, (R)P.sigma, scl);
   const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
   gs *__restrict__ go = (gs *)S.g_out;
   us *__restrict__ uo = (us *)S.u_out;
@@ -1058,9 +1082,9 @@ __device__ __forceinline__ void tma_tile(const Params &P, const StepPtrs &S, con
     for (int q = 0; q < 9; ++q) f[q] = G(q, gr - ey(q), gc - ex(q));
     const int rx = lx + 1, ry = ly + 1;
     auto n = [&](int m, int yy, int xx) -> R { return snb[(m * H1 + yy) * W1 + xx]; };
-    const R Sx = fmr(n(0, ry, rx + 1) - n(0, ry, rx - 1), hdx, (n(1, ry + 1, rx) - n(1, ry - 1, rx)) * hdx) + sbx;
-    const R Sy = fmr(n(2, ry, rx + 1) - n(2, ry, rx - 1), hdx, (n(3, ry + 1, rx) - n(3, ry - 1, rx)) * hdx) + sby;
-    collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
+    const R Sx = fmr(n(0, ry, rx + 1) - n(0, ry, rx - 1), hdx, fmr(n(1, ry + 1, rx) - n(1, ry - 1, rx), hdx, sbx));
+    const R Sy = fmr(n(2, ry, rx + 1) - n(2, ry, rx - 1), hdx, fmr(n(3, ry + 1, rx) - n(3, ry - 1, rx), hdx, sby));
+    collide<R>(f, Sx, Sy, K);
     const size_t idx = (size_t)(y0 + ly) * P.pitch + (x0 + lx);
 #pragma unroll
     for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[q], scl);
@@ -1304,7 +1328,8 @@ __device__ __forceinline__ void fused2_tile(const Params &P, const StepPtrs &S, 
   using gs = typename C::gs;
   const R inv = gscale_inv<gs, R>(P), scl = gscale<gs, R>(P);
   const R kap = (R)P.kappa * inv, hdx = R(0.5) * (R)P.inv_dx;
-  const R lam = (R)P.lam, mu = (R)P.mu, omega = (R)P.omega, sigma = (R)P.sigma;
+  const R lam = (R)P.lam, mu = (R)P.mu;
+  const CollideK<R> K = collide_k<R>((R)P.omega, (R)P.sigma, scl);
   const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
   // u(t+dt) at node offset (i, j) from the populations of array A (g box or g1)
   auto advance_u = [&](auto A, int i, int j) {
@@ -1318,7 +1343,7 @@ __device__ __forceinline__ void fused2_tile(const Params &P, const StepPtrs &S, 
     first_moment(o, gx, gy);
     first_moment(p, fx, fy);
     us &uu = su[F::u(i, j)];
-    uu = uadd(uu, kap * (gx + fx), kap * (gy + fy));
+    uu = uadd_k(uu, kap, gx + fx, gy + fy);
   };
   // N at node offset (i, j) from u in the u box
   auto stress = [&](int i, int j) {
@@ -1338,9 +1363,9 @@ __device__ __forceinline__ void fused2_tile(const Params &P, const StepPtrs &S, 
 #pragma unroll
     for (int q = 0; q < 9; ++q) f[q] = A(q, i - ex(q), j - ey(q));
     auto n = [&](int m, int ii, int jj) -> R { return sn[F::n(m, ii, jj)]; };
-    const R Sx = fmr(n(0, i + 1, j) - n(0, i - 1, j), hdx, (n(1, i, j + 1) - n(1, i, j - 1)) * hdx) + sbx;
-    const R Sy = fmr(n(2, i + 1, j) - n(2, i - 1, j), hdx, (n(3, i, j + 1) - n(3, i, j - 1)) * hdx) + sby;
-    collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
+    const R Sx = fmr(n(0, i + 1, j) - n(0, i - 1, j), hdx, fmr(n(1, i, j + 1) - n(1, i, j - 1), hdx, sbx));
+    const R Sy = fmr(n(2, i + 1, j) - n(2, i - 1, j), hdx, fmr(n(3, i, j + 1) - n(3, i, j - 1), hdx, sby));
+    collide<R>(f, Sx, Sy, K);
   };
   auto Gk = [&](int q, int i, int j) -> R { return fconv<F>(sg[F::g(q, i, j)]); };
   auto G1 = [&](int q, int i, int j) -> R { return fconv<F>(sh[F::h(q, i, j)]); };
@@ -1609,7 +1634,8 @@ __global__ void __launch_bounds__(M::NT) step_march_kernel(const Params P, const
 
   const R inv = gscale_inv<gs, R>(P), scl = gscale<gs, R>(P);
   const R kap = (R)P.kappa * inv, hdx = R(0.5) * (R)P.inv_dx;
-  const R lam = (R)P.lam, mu = (R)P.mu, omega = (R)P.omega, sigma = (R)P.sigma;
+  const R lam = (R)P.lam, mu = (R)P.mu;
+  const CollideK<R> K = collide_k<R>((R)P.omega, (R)P.sigma, scl);
   const R sbx = (R)(P.rho0 * P.body[0]), sby = (R)(P.rho0 * P.body[1]);
   const size_t plane = (size_t)P.ny * P.pitch;
   gs *__restrict__ go = (gs *)S.g_out;
@@ -1629,7 +1655,7 @@ __global__ void __launch_bounds__(M::NT) step_march_kernel(const Params P, const
       first_moment(o, gx, gy);
       first_moment(p, fx, fy);
       us &uu = U(row, cx);
-      uu = uadd(uu, kap * (gx + fx), kap * (gy + fy));
+      uu = uadd_k(uu, kap, gx + fx, gy + fy);
     }
   };
   // N for rows [r0, r0 + nrow) (x: x0-1 .. x0+TX)
@@ -1700,9 +1726,9 @@ __global__ void __launch_bounds__(M::NT) step_march_kernel(const Params P, const
       R f[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) f[q] = G(q, row - ey(q), gc - ex(q));
-      const R Sx = fmr(N(0, row, rx + 1) - N(0, row, rx - 1), hdx, (N(1, row + 1, rx) - N(1, row - 1, rx)) * hdx) + sbx;
-      const R Sy = fmr(N(2, row, rx + 1) - N(2, row, rx - 1), hdx, (N(3, row + 1, rx) - N(3, row - 1, rx)) * hdx) + sby;
-      collide<R>(f, Sx * scl, Sy * scl, omega, sigma);
+      const R Sx = fmr(N(0, row, rx + 1) - N(0, row, rx - 1), hdx, fmr(N(1, row + 1, rx) - N(1, row - 1, rx), hdx, sbx));
+      const R Sy = fmr(N(2, row, rx + 1) - N(2, row, rx - 1), hdx, fmr(N(3, row + 1, rx) - N(3, row - 1, rx), hdx, sby));
+      collide<R>(f, Sx, Sy, K);
       const size_t idx = (size_t)row * P.pitch + (x0 + lx);
 #pragma unroll
       for (int q = 0; q < 9; ++q) gstore(go, q * plane + idx, f[q], scl);
@@ -1849,9 +1875,7 @@ __global__ void __launch_bounds__(C::NT) init_kernel(const Params P, typename C:
     const int lx = tx, ly = ty + i * C::NTY, x = x0 + lx, y = y0 + ly;
     if (x >= P.nx || y >= P.ny) continue;
     R Sx, Sy, H[4];
-    Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
-    Sx += (R)(P.rho0 * P.body[0]);
-    Sy += (R)(P.rho0 * P.body[1]);
+    Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, (R)(P.rho0 * P.body[0]), (R)(P.rho0 * P.body[1]), Sx, Sy);
     Fd<C, true>::grad(sm, P, lx + 1, ly + 1, x, y, idx_, H);
     const size_t i0 = (size_t)y * P.nx + x;
     const R trH = H[0] + H[3];
@@ -1870,7 +1894,7 @@ __global__ void __launch_bounds__(C::NT) init_kernel(const Params P, typename C:
       const R eAe = R(ex(q) * ex(q)) * Axx + R(2 * ex(q) * ey(q)) * Axy + R(ey(q) * ey(q)) * Ayy;
       f[q] = wq<R>(q) * (rq + R(ex(q)) * jx + R(ey(q)) * jy + R(1.5) * eAe - R(0.5) * (Axx + Ayy)) * scl;
     }
-    collide<R>(f, Sx * scl, Sy * scl, (R)P.omega, (R)P.sigma);
+    collide<R>(f, Sx, Sy, collide_k<R>((R)P.omega, (R)P.sigma, scl));
     const size_t idx = (size_t)y * P.pitch + x;
     for (int q = 0; q < 9; ++q) gstore(g, q * plane + idx, f[q], scl);
     u[idx] = sm.u[ly + 2][lx + 2];
@@ -1902,9 +1926,7 @@ __global__ void __launch_bounds__(C::NT) fields_kernel(const Params P, const typ
     }
     if (vo) {
       R Sx, Sy;
-      Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
-      Sx += (R)(P.rho0 * P.body[0]);
-      Sy += (R)(P.rho0 * P.body[1]);
+      Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, (R)(P.rho0 * P.body[0]), (R)(P.rho0 * P.body[1]), Sx, Sy);
       R gq[9], m1x, m1y;
       for (int q = 1; q < 9; ++q) gq[q] = gload(g, q * plane + idx, inv);
       first_moment(gq, m1x, m1y);

@@ -80,9 +80,7 @@ __global__ void __launch_bounds__(C::NT) fields_rows_kernel(const Params P, cons
     }
     if (vo) {
       R Sx, Sy;
-      Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, Sx, Sy);
-      Sx += (R)(P.rho0 * P.body[0]);
-      Sy += (R)(P.rho0 * P.body[1]);
+      Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, (R)(P.rho0 * P.body[0]), (R)(P.rho0 * P.body[1]), Sx, Sy);
       R gq[9], m1x, m1y;
       for (int q = 1; q < 9; ++q) gq[q] = gload(g, q * plane + idx, inv);
       first_moment(gq, m1x, m1y);

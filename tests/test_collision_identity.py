@@ -27,7 +27,9 @@ def literal(O, f, S, cs, tau, dt):
 
 
 def ghost(f, S, cs, tau, dt):
-    """The kernels' form: g_q = f_q - omega (f - feq)_q + w_q sigma e_q.S."""
+    """The kernels' form: g_q = f_q - omega (f - feq)_q + w_q sigma e_q.S, each
+    opposite pair as (f + A) +- b with A the relaxation of the even part and b
+    that of the odd part plus the forcing."""
     c = math.sqrt(3.0) * cs
     omega, sigma = 1.0 / tau, c * dt / cs ** 2
     s13, s24, s57, s68 = f[1] + f[3], f[2] + f[4], f[5] + f[7], f[6] + f[8]
@@ -35,15 +37,18 @@ def ghost(f, S, cs, tau, dt):
     Q = f[0] - 2 * (s13 + s24) + 4 * (s57 + s68)
     ox, oy = d13 / 6 - (d57 - d68) / 3, d24 / 6 - (d57 + d68) / 3
     o57, o68 = d57 / 3 - (d13 + d24) / 12, d68 / 3 - (d24 - d13) / 12
-    ne0, ne1, ne5 = Q / 9, -Q / 18, Q / 36
-    fx, fy = sigma * S[0] / 9, sigma * S[1] / 9
-    f57, f68 = sigma * (S[0] + S[1]) / 36, sigma * (S[1] - S[0]) / 36
+    fx, fy = S[0] * (sigma / 9), S[1] * (sigma / 9)
+    f57, f68 = (S[0] + S[1]) * (sigma / 36), (S[1] - S[0]) * (sigma / 36)
+    # even relaxation shared by a pair, odd part and forcing with opposite signs
+    A1, A5 = Q * (omega / 18), Q * (-omega / 36)
+    bx, by = -omega * ox + fx, -omega * oy + fy
+    b57, b68 = -omega * o57 + f57, -omega * o68 + f68
     g = np.empty(9)
-    g[0] = f[0] - omega * ne0
-    g[1], g[3] = f[1] - omega * (ne1 + ox) + fx, f[3] - omega * (ne1 - ox) - fx
-    g[2], g[4] = f[2] - omega * (ne1 + oy) + fy, f[4] - omega * (ne1 - oy) - fy
-    g[5], g[7] = f[5] - omega * (ne5 + o57) + f57, f[7] - omega * (ne5 - o57) - f57
-    g[6], g[8] = f[6] - omega * (ne5 + o68) + f68, f[8] - omega * (ne5 - o68) - f68
+    g[0] = f[0] - omega * (Q / 9)
+    g[1], g[3] = (f[1] + A1) + bx, (f[3] + A1) - bx
+    g[2], g[4] = (f[2] + A1) + by, (f[4] + A1) - by
+    g[5], g[7] = (f[5] + A5) + b57, (f[7] + A5) - b57
+    g[6], g[8] = (f[6] + A5) + b68, (f[8] + A5) - b68
     return g
 
 
