@@ -843,14 +843,30 @@ __global__ void __launch_bounds__(FrameCfg<C, SPLIT>::type::NT) batch_step_kerne
   batch_walk<C, EDGE, LIN, SPLIT>(lats, tiles, ntiles, it, err);
 }
 
-// The same walk over frame tiles (own wall values), held to three blocks per
-// SM: a frame tile waits on the latency of its global loads, and a third
-// block per SM hides more of it than the registers it gives up cost (single
-// precision; the FP16-storage and FP64 frame code would spill)
+// The same walks held to more blocks per SM (single precision): a batch tile
+// waits on the latency of its global loads, and another block per SM hides
+// more of it than the registers it gives up cost.  Interior tiles: four
+// blocks (64 registers, no spills); frame tiles with own wall values: three
+// (80 registers).  The FP16-storage and FP64 code would spill.
+template <class C>
+__global__ void __launch_bounds__(C::NT, 4) batch_interior4_kernel(const BatchLattice *lats, const BatchTile *tiles,
+                                                                   int ntiles, int it, int *err) {
+  batch_walk<C, false, false, false>(lats, tiles, ntiles, it, err);
+}
 template <class C>
 __global__ void __launch_bounds__(C::NT, 3) batch_frame3_kernel(const BatchLattice *lats, const BatchTile *tiles,
                                                                 int ntiles, int it, int *err) {
   batch_walk<C, true, false, false>(lats, tiles, ntiles, it, err);
+}
+
+// resident blocks of a batch kernel on this device
+template <class C>
+int batch_resident(void (*kernel)(const BatchLattice *, const BatchTile *, int, int, int *)) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, C::NT, 0);
+  return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
 }
 
 // launch `it` of a chunk: the interior tiles and the frame tiles of every
@@ -859,21 +875,27 @@ template <class C>
 cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *interior, int ni, const BatchTile *edge,
                               int ne, const BatchTile *edge_lin, int nl, int it, int *err, cudaStream_t st,
                               const StreamFork *fork) {
-  // resident blocks of the persistent kernel on this device (computed once;
-  // the initialisation of a function-local static is thread-safe)
-  static const int blocks = [] {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<C, false>, C::NT, 0);
-    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
-  }();
+  using KFn = void (*)(const BatchLattice *, const BatchTile *, int, int, int *);
+  // single precision: the interior and own-value frame walks held to four
+  // and three blocks per SM (the other precisions would spill)
+  KFn ki, kf;
+  if constexpr (sizeof(typename C::gs) == 4 && sizeof(typename C::real) == 4) {
+    ki = batch_interior4_kernel<C>;
+    kf = batch_frame3_kernel<C>;
+  } else {
+    ki = batch_step_kernel<C, false>;
+    kf = batch_step_kernel<C, true>;
+  }
+  const KFn kl = batch_step_kernel<C, true, true>;
+  // resident blocks of each persistent walk (computed once; the
+  // initialisation of a function-local static is thread-safe)
+  static const int bi = batch_resident<C>(ki), bf = batch_resident<C>(kf), bl = batch_resident<C>(kl);
   // the frame tiles (few, long, latency-bound) run beside the interior tiles
   // when a side stream is given and the interior walk is short (beside a
   // long persistent walk they would hold back blocks whose tiles are fixed):
   // both read iteration k and write k + 1 of disjoint nodes; the counters
   // advance once both have finished
-  const bool split = fork && ni > 0 && ni <= kForkWalk * blocks && (ne > 0 || nl > 0);
+  const bool split = fork && ni > 0 && ni <= kForkWalk * bi && (ne > 0 || nl > 0);
   // no more frame tiles than SMs: run each as CPT blocks of one node per
   // thread (the frame launch is then the iteration's critical path)
   static const int sms = [] {
@@ -892,21 +914,15 @@ cudaError_t launch_batch_step(BatchLattice *lats, int nlats, const BatchTile *in
         return;
       }
     }
-    if (ne > 0) {
-      if constexpr (sizeof(typename C::gs) == 4 && sizeof(typename C::real) == 4)
-        batch_frame3_kernel<C><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, it, err);
-      else
-        batch_step_kernel<C, true><<<ne < blocks ? ne : blocks, C::NT, 0, fs>>>(lats, edge, ne, it, err);
-    }
-    if (nl > 0)
-      batch_step_kernel<C, true, true><<<nl < blocks ? nl : blocks, C::NT, 0, fs>>>(lats, edge_lin, nl, it, err);
+    if (ne > 0) kf<<<ne < bf ? ne : bf, C::NT, 0, fs>>>(lats, edge, ne, it, err);
+    if (nl > 0) kl<<<nl < bl ? nl : bl, C::NT, 0, fs>>>(lats, edge_lin, nl, it, err);
   };
   if (split) {
     cudaEventRecord(fork->fork, st);
     cudaStreamWaitEvent(fork->side, fork->fork, 0);
     frame(fork->side);
   }
-  if (ni > 0) batch_step_kernel<C, false><<<ni < blocks ? ni : blocks, C::NT, 0, st>>>(lats, interior, ni, it, err);
+  if (ni > 0) ki<<<ni < bi ? ni : bi, C::NT, 0, st>>>(lats, interior, ni, it, err);
   if (!split) frame(st);
   if (split) {
     cudaEventRecord(fork->join, fork->side);
