@@ -986,7 +986,11 @@ struct TmaCfg : TmaGeom<C::TX, C::TY, (int)sizeof(typename C::gs), (int)sizeof(t
   using us = typename C::us;
   using real = typename C::real;
   static constexpr int TX = C::TX, TY = C::TY, GW = B::GW, GH = B::GH, UW = B::UW, UH = B::UH, XO = B::XO;
+  // the u map copies 16-byte records as pairs of 8-byte elements (a raw
+  // copy), so a box row holds 2 UW elements: at most 128 records
   static constexpr int UEL = (int)(sizeof(us) / sizeof(real)); // reals per u record (2 or 4)
+  static constexpr int UQ = (int)(sizeof(us) / 8);
+  static_assert(UQ * UW <= 256, "a TMA box row holds at most 256 elements");
   static constexpr size_t G_BYTES = (size_t)9 * GH * GW * sizeof(gs);
   static constexpr size_t U_BYTES = (size_t)UH * UW * sizeof(us);
   static constexpr size_t N_BYTES = (size_t)4 * (TY + 2) * (TX + 2) * sizeof(real);
@@ -1127,7 +1131,7 @@ __global__ void __launch_bounds__(C::NT) step_tma_kernel(const Params P, const S
     mbar_init(bar, 1);
     mbar_expect_tx(bar, (uint32_t)(T::G_BYTES + T::U_BYTES));
     tma_load_3d(sg, &tm_g, x0 - T::XO, y0 - 3, 0, bar);
-    tma_load_2d(su, &tm_u, T::UEL * (x0 - 2), y0 - 2, bar);
+    tma_load_2d(su, &tm_u, T::UQ * (x0 - 2), y0 - 2, bar);
   }
   __syncthreads();  // the barrier is initialised before anyone polls it
   int ok = 0;
@@ -1187,7 +1191,7 @@ __device__ __forceinline__ void tma2_issue(unsigned char *stage, uint64_t *bar, 
   using T = TmaCfg<C>;
   mbar_expect_tx(bar, (uint32_t)(T::G_BYTES + T::U_BYTES));
   tma_load_3d(stage, &tm_g, x0 - T::XO, y0 - 3, 0, bar);
-  tma_load_2d(stage + T::OFF_U, &tm_u, T::UEL * (x0 - 2), y0 - 2, bar);
+  tma_load_2d(stage + T::OFF_U, &tm_u, T::UQ * (x0 - 2), y0 - 2, bar);
 }
 
 template <class C>
@@ -1835,11 +1839,10 @@ bool make_tma_maps(const Params &P, const void *g, const void *u, void *out_g, v
   CUresult r1 = encode((CUtensorMap *)out_g, gt, 3, const_cast<void *>(g), gdim, gstr, gbox, est,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  const CUtensorMapDataType ut = sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const cuuint64_t udim[2] = {(cuuint64_t)T::UEL * P.pitch, (cuuint64_t)P.ny};
-  const cuuint64_t ustr[1] = {(cuuint64_t)T::UEL * P.pitch * sizeof(R)};
-  const cuuint32_t ubox[2] = {(cuuint32_t)(T::UEL * T::UW), (cuuint32_t)T::UH};
-  CUresult r2 = encode((CUtensorMap *)out_u, ut, 2, const_cast<void *>(u), udim, ustr, ubox, est,
+  const cuuint64_t udim[2] = {(cuuint64_t)T::UQ * P.pitch, (cuuint64_t)P.ny};
+  const cuuint64_t ustr[1] = {(cuuint64_t)T::UQ * P.pitch * 8};
+  const cuuint32_t ubox[2] = {(cuuint32_t)(T::UQ * T::UW), (cuuint32_t)T::UH};
+  CUresult r2 = encode((CUtensorMap *)out_u, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(u), udim, ustr, ubox, est,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return false;
