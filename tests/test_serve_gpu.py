@@ -43,7 +43,7 @@ def alone(L, case):
         return s.fields()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16s"])
 def test_mixed_batch_equals_alone(L, precision):
     cases = mix(precision)
     with L.Server(precision=precision, chunk=32) as srv:
