@@ -158,9 +158,11 @@ __host__ __device__ __forceinline__ void first_moment(const R v[9], R &mx, R &my
 //   NH : with a = J - 1 = trH + detH, K = trH I - H^T (cof F = I + K),
 //        N = (mu/J) (-a H^T + (a - (2 + a) trH) I) + lam a (a + 2) / (2 J) (I + K)
 //   LE : N = (lam - mu) trH I
-// H = (H11, H12, H21, H22), H_ab = d u_a / d X_b.
+// H = (H11, H12, H21, H22), H_ab = d u_a / d X_b.  Returns false, with N
+// unset, for neo-Hooke where J < jmin (the caller then evaluates the law in
+// a wider type); the default jmin never refuses.
 template <class R>
-__host__ __device__ inline void constitutive_n(int model, R lam, R mu, const R H[4], R N[4]) {
+__host__ __device__ inline bool constitutive_n(int model, R lam, R mu, const R H[4], R N[4], R jmin = R(-INFINITY)) {
   const R h11 = H[0], h12 = H[1], h21 = H[2], h22 = H[3];
   const R trH = h11 + h22;
   if (model == LBS_LE) {
@@ -186,6 +188,7 @@ __host__ __device__ inline void constitutive_n(int model, R lam, R mu, const R H
     const R detH = fmr(h11, h22, -(h12 * h21));
     const R a = trH + detH;
     const R J = R(1) + a;
+    if (J < jmin) return false;
     const R iJ = R(1) / J;
     const R m = mu * iJ;
     const R l = R(0.5) * lam * a * (a + R(2)) * iJ;
@@ -197,22 +200,22 @@ __host__ __device__ inline void constitutive_n(int model, R lam, R mu, const R H
     N[2] = -((ma + l) * h12);
     N[3] = fmr(-ma, h22, fmr(l, R(1) + h11, diag));
   }
+  return true;
 }
 
 // N in the compute type; the FP32 kernels evaluate neo-Hooke in double where
-// J is small (near det F -> 0 the 1/J terms lose float accuracy)
+// J < 1/2 (near det F -> 0 the 1/J terms lose float accuracy)
 template <class R>
 __device__ __forceinline__ void material(const Params &P, R lam, R mu, const R H[4], R N[4]) {
-  if (sizeof(R) == 4 && P.model == LBS_NH) {
-    const R J = R(1) + ((H[0] + H[3]) + fmr(H[0], H[3], -(H[1] * H[2])));
-    if (J < R(0.5)) {
+  if constexpr (sizeof(R) == 4) {
+    if (!constitutive_n<R>(P.model, lam, mu, H, N, R(0.5))) {
       double Hd[4] = {H[0], H[1], H[2], H[3]}, Nd[4];
       constitutive_n<double>(P.model, P.lam, P.mu, Hd, Nd);
       for (int m = 0; m < 4; ++m) N[m] = (R)Nd[m];
-      return;
     }
+  } else {
+    constitutive_n<R>(P.model, lam, mu, H, N);
   }
-  constitutive_n<R>(P.model, lam, mu, H, N);
 }
 
 // ------------------------------------------------------------------ loads
