@@ -26,7 +26,7 @@ def literal(O, f, S, cs, tau, dt):
     return f - (f - feq) / tau + (1.0 - 0.5 / tau) * psi * dt
 
 
-def ghost(f, S, cs, tau, dt):
+def ghost(f, S, cs, tau, dt, scaled_odd=True):
     """The kernels' form: g_q = f_q - omega (f - feq)_q + w_q sigma e_q.S, each
     opposite pair as (f + A) +- b with A the relaxation of the even part and b
     that of the odd part plus the forcing."""
@@ -35,14 +35,20 @@ def ghost(f, S, cs, tau, dt):
     s13, s24, s57, s68 = f[1] + f[3], f[2] + f[4], f[5] + f[7], f[6] + f[8]
     d13, d24, d57, d68 = f[1] - f[3], f[2] - f[4], f[5] - f[7], f[6] - f[8]
     Q = f[0] - 2 * (s13 + s24) + 4 * (s57 + s68)
-    ox, oy = d13 / 6 - (d57 - d68) / 3, d24 / 6 - (d57 + d68) / 3
-    o57, o68 = d57 / 3 - (d13 + d24) / 12, d68 / 3 - (d24 - d13) / 12
     fx, fy = S[0] * (sigma / 9), S[1] * (sigma / 9)
     f57, f68 = (S[0] + S[1]) * (sigma / 36), (S[1] - S[0]) * (sigma / 36)
     # even relaxation shared by a pair, odd part and forcing with opposite signs
     A1, A5 = Q * (omega / 18), Q * (-omega / 36)
-    bx, by = -omega * ox + fx, -omega * oy + fy
-    b57, b68 = -omega * o57 + f57, -omega * o68 + f68
+    if scaled_odd:  # (double precision) the odd parts times 6 and 12, the factor -omega/6, -omega/12
+        tx, ty = d13 - 2 * (d57 - d68), d24 - 2 * (d57 + d68)
+        t57, t68 = 4 * d57 - (d13 + d24), 4 * d68 - (d24 - d13)
+        bx, by = tx * (-omega / 6) + fx, ty * (-omega / 6) + fy
+        b57, b68 = t57 * (-omega / 12) + f57, t68 * (-omega / 12) + f68
+    else:  # (single precision) the odd parts themselves
+        ox, oy = d13 / 6 - (d57 - d68) / 3, d24 / 6 - (d57 + d68) / 3
+        o57, o68 = d57 / 3 - (d13 + d24) / 12, d68 / 3 - (d24 - d13) / 12
+        bx, by = -omega * ox + fx, -omega * oy + fy
+        b57, b68 = -omega * o57 + f57, -omega * o68 + f68
     g = np.empty(9)
     g[0] = f[0] - omega * (Q / 9)
     g[1], g[3] = (f[1] + A1) + bx, (f[3] + A1) - bx
@@ -52,8 +58,9 @@ def ghost(f, S, cs, tau, dt):
     return g
 
 
+@pytest.mark.parametrize("scaled_odd", [True, False])
 @pytest.mark.parametrize("seed", range(20))
-def test_ghost_form_equals_literal_collision(oracle_mod, seed):
+def test_ghost_form_equals_literal_collision(oracle_mod, seed, scaled_odd):
     rng = np.random.default_rng(seed)
     f = rng.normal(0.0, 0.1, 9)
     S = rng.normal(0.0, 1.0, 2)
@@ -61,7 +68,7 @@ def test_ghost_form_equals_literal_collision(oracle_mod, seed):
     tau = rng.uniform(0.51, 1.5)
     dt = rng.uniform(0.01, 0.1)
     ref = literal(oracle_mod, f, S, cs, tau, dt)
-    assert np.abs(ghost(f, S, cs, tau, dt) - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max())
+    assert np.abs(ghost(f, S, cs, tau, dt, scaled_odd) - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max())
 
 
 def test_ghost_form_conserves_r_pi_and_adds_dt_s(oracle_mod):
