@@ -832,13 +832,20 @@ __device__ __forceinline__ void batch_walk(const BatchLattice *lats, const Batch
   __shared__ Params sP;
   __shared__ StepPtrs sS;
   __shared__ int skip;
+  static_assert(sizeof(Params) % 8 == 0, "the tile header is copied in 8-byte words");
   for (int t = blockIdx.x; t < ntiles * parts; t += gridDim.x) {
-    if (threadIdx.x == 0) {
+    // the tile's lattice header, read by the first warp: every lane reads the
+    // entry and the counters (one broadcast each) and copies a share of the
+    // parameters, so the copy costs one round trip instead of one per word
+    if (threadIdx.x < 32) {
       const BatchTile T = tiles[t / parts];
       const BatchLattice &L = lats[T.lat];
-      skip = L.k + it >= L.kend;
-      if (!skip) {
-        sP = L.P;
+      const bool sk = L.k + it >= L.kend;
+      if (!sk)
+        for (int w = threadIdx.x; w < (int)(sizeof(Params) / 8); w += 32)
+          ((long long *)&sP)[w] = ((const long long *)&L.P)[w];
+      if (threadIdx.x == 0) skip = sk;
+      if (threadIdx.x == 0 && !sk) {
         const int p = (int)((L.k + it) & 1);
         sS.g_in = L.g[p];
         sS.g_out = L.g[p ^ 1];
