@@ -251,6 +251,7 @@ StepPtrs ptrs(const lbs_handle *h, int parity, const int64_t *kptr, int64_t koff
   s.tm_u = h->tma ? (const void *)&h->tm_u[parity] : nullptr;
   s.err = h->errdev;
   s.fork = h->fork.side ? &h->fork : nullptr;
+  s.sev = nullptr;
   return s;
 }
 

@@ -649,7 +649,11 @@ __device__ __forceinline__ void step_tile(const Params &P, const StepPtrs &S, in
   // tile (the wall rules of every wall node read them)
   __shared__ double sev[4][2];
   if (EDGE) {
-    if (threadIdx.x < 4) edge_value(P, threadIdx.x, k, sev[threadIdx.x]);
+    if (S.sev) {
+      if (threadIdx.x < 8) sev[threadIdx.x >> 1][threadIdx.x & 1] = S.sev[threadIdx.x];
+    } else if (threadIdx.x < 4) {
+      edge_value(P, threadIdx.x, k, sev[threadIdx.x]);
+    }
     __syncthreads();
   }
   // g is held in units of g * 2^gshift (1 unless FP16 storage)
@@ -858,6 +862,7 @@ __device__ __forceinline__ void batch_walk(const BatchLattice *lats, const Batch
         sS.tm_g = sS.tm_u = nullptr;
         sS.err = err;
         sS.fork = nullptr;
+        sS.sev = L.sev ? L.sev + (size_t)it * 8 : nullptr;
       }
     }
     __syncthreads();

@@ -58,6 +58,8 @@ struct StepPtrs {
   const void *tm_u;     //   u_in (TMA tile variants only)
   int *err;             // device flag set when a bounded wait gives up
   const StreamFork *fork;  // host: run the frame tiles beside the interior tiles (or null)
+  const double *sev;    // the four edges' prescribed values at this iteration ([4][2],
+                        //   device), or null: the frame tiles evaluate them
 };
 
 struct TileShape {
@@ -73,11 +75,14 @@ struct BatchLattice {
                  // chunk steps iteration k + it, buffers [(k + it) & 1]); advanced
                  // on the device once per chunk (launch_batch_advance)
   int64_t kend;  // the lattice stops here (its tiles return at once)
+  double *sev;   // the edges' prescribed values for the iterations of the chunk,
+                 // [it][4][2] (filled once per chunk, launch_batch_edges)
 };
 
 // advance every lattice's chunk-start iteration by a chunk of n launches
 // (to its end at most); one launch
 cudaError_t launch_batch_advance(BatchLattice *lats, int nlats, int n, cudaStream_t st);
+cudaError_t launch_batch_edges(BatchLattice *lats, int nlats, int n, cudaStream_t st);
 
 // One tile of a batch: lattice index and tile coordinates (in tiles).
 struct BatchTile {

@@ -36,6 +36,23 @@ cudaError_t launch_batch_advance(BatchLattice *lats, int nlats, int n, cudaStrea
   return cudaGetLastError();
 }
 
+// the edges' prescribed values of every lattice for the n iterations of the
+// chunk (iteration k + it, k its chunk start), with the frame tiles' own
+// function: one thread per lattice, iteration and edge
+static __global__ void batch_edges_kernel(BatchLattice *lats, int nlats, int n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nlats * n * 4) return;
+  const int e = (int)(i % 4), it = (int)((i / 4) % n), l = (int)(i / (4 * (int64_t)n));
+  const BatchLattice &L = lats[l];
+  if (L.sev) edge_value(L.P, e, L.k + it, L.sev + ((size_t)it * 4 + e) * 2);
+}
+
+cudaError_t launch_batch_edges(BatchLattice *lats, int nlats, int n, cudaStream_t st) {
+  const int64_t m = (int64_t)nlats * n * 4;
+  if (m > 0) batch_edges_kernel<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(lats, nlats, n);
+  return cudaGetLastError();
+}
+
 }  // namespace lbs
 
 namespace {
@@ -83,6 +100,8 @@ struct lbs_server {
   int lat_cap = 0;
   BatchTile *d_tiles = nullptr;
   int tile_cap = 0;
+  double *d_sev = nullptr;  // the chunk's edge values, [lattice][it][4][2]
+  int sev_cap = 0;
   int *d_err = nullptr;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -202,6 +221,8 @@ struct ChunkGraph {
 cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int shape, int nres, int ni, int ne, int nl, int64_t n,
                       ChunkGraph &G) {
   auto direct = [&]() -> cudaError_t {
+    const cudaError_t e0 = lbs::launch_batch_edges(s->d_lats, nres, (int)n, s->stream);
+    if (e0 != cudaSuccess) return e0;
     for (int64_t it = 0; it < n; ++it) {
       const BatchTile *t = s->d_tiles;
       const cudaError_t e = L.batch_step(shape, s->d_lats, nres, t, ni, t + ni, ne, t + ni + ne, nl, (int)it,
@@ -449,6 +470,7 @@ void run(lbs_server *s) {
         }
         B.k = res[i]->k;
         B.kend = res[i]->nsteps;
+        B.sev = nullptr;  // set once the table is allocated
         const int ntx = (h->P.nx + TX - 1) / TX, nty = (h->P.ny + TY - 1) / TY;
         int a_lo, a_hi, b_lo, b_hi;
         lbs::interior_range(h->P.nx, h->P.ny, TX, TY, a_lo, a_hi, b_lo, b_hi);
@@ -463,6 +485,9 @@ void run(lbs_server *s) {
       nl = (int)edge_lin.size();
       ht.insert(ht.end(), edge.begin(), edge.end());
       ht.insert(ht.end(), edge_lin.begin(), edge_lin.end());
+      const int sev_need = (int)hl.size() * (int)s->cfg.chunk * 8;
+      const bool sev_ok = ensure(s->d_sev, s->sev_cap, sev_need);
+      for (size_t i = 0; i < hl.size(); ++i) hl[i].sev = sev_ok ? s->d_sev + i * (size_t)s->cfg.chunk * 8 : nullptr;
       if (!ensure(s->d_lats, s->lat_cap, (int)hl.size()) || !ensure(s->d_tiles, s->tile_cap, (int)ht.size())) {
         for (Req *r : res) retire.emplace_back(r, LBS_ENOMEM);
         res.clear();
@@ -678,6 +703,7 @@ int lbs_server_destroy(lbs_server *s) {
   }
   if (s->d_lats) cudaFree(s->d_lats);
   if (s->d_tiles) cudaFree(s->d_tiles);
+  if (s->d_sev) cudaFree(s->d_sev);
   if (s->d_err) cudaFree(s->d_err);
   if (s->stream) cudaStreamDestroy(s->stream);
   if (s->fork.side) cudaStreamDestroy(s->fork.side);
