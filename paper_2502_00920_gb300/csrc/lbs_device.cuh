@@ -835,6 +835,7 @@ __device__ __forceinline__ void batch_walk(const BatchLattice *lats, const Batch
   constexpr int parts = C::TY / H::TY;
   __shared__ Params sP;
   __shared__ StepPtrs sS;
+  __shared__ BatchTile sT;
   __shared__ int skip;
   static_assert(sizeof(Params) % 8 == 0, "the tile header is copied in 8-byte words");
   for (int t = blockIdx.x; t < ntiles * parts; t += gridDim.x) {
@@ -848,7 +849,10 @@ __device__ __forceinline__ void batch_walk(const BatchLattice *lats, const Batch
       if (!sk)
         for (int w = threadIdx.x; w < (int)(sizeof(Params) / 8); w += 32)
           ((long long *)&sP)[w] = ((const long long *)&L.P)[w];
-      if (threadIdx.x == 0) skip = sk;
+      if (threadIdx.x == 0) {
+        skip = sk;
+        sT = T;
+      }
       if (threadIdx.x == 0 && !sk) {
         const int p = (int)((L.k + it) & 1);
         sS.g_in = L.g[p];
@@ -866,10 +870,7 @@ __device__ __forceinline__ void batch_walk(const BatchLattice *lats, const Batch
       }
     }
     __syncthreads();
-    if (!skip) {
-      const BatchTile T = tiles[t / parts];
-      step_tile<H, EDGE, LIN>(sP, sS, T.a * C::TX, T.b * C::TY + (t % parts) * H::TY);
-    }
+    if (!skip) step_tile<H, EDGE, LIN>(sP, sS, sT.a * C::TX, sT.b * C::TY + (t % parts) * H::TY);
     __syncthreads();  // the next tile reuses the shared memory
   }
 }
