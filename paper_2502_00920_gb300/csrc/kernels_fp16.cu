@@ -1,5 +1,6 @@
 // FP16 storage (scaled), FP32 arithmetic, u as a float pair: kernel instantiations and launchers of liblbs.
 #include "lbs_device.cuh"
+#include "lbs_batch.cuh"
 
 namespace lbs {
 namespace {

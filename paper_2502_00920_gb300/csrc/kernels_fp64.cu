@@ -1,5 +1,6 @@
 // FP64 storage and arithmetic: kernel instantiations and launchers of liblbs.
 #include "lbs_device.cuh"
+#include "lbs_batch.cuh"
 
 namespace lbs {
 namespace {
