@@ -7,8 +7,10 @@
  * requests while their device footprint (lbs_footprint) fits the HBM budget,
  * keeps the admitted lattices' state resident, and advances all of them
  * together: every iteration launches batched kernels that walk tile tables
- * spanning all resident lattices (interior tiles, frame tiles), and once per
- * chunk one launch advances their iteration counters.  The worker runs `chunk`
+ * spanning all resident lattices (interior tiles, frame tiles); once per
+ * chunk one launch evaluates the edges' prescribed values of every lattice for
+ * the chunk's iterations and one advances their iteration counters.  The
+ * worker runs `chunk`
  * iterations between scheduling points; a lattice that reaches
  * its iteration count stops (its tiles return at once), is checked for
  * non-finite values, has u, v and P copied to host memory owned by the server
