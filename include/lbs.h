@@ -48,6 +48,7 @@ extern "C" {
 #define LBS_ETIMEOUT (-5)  /* a bounded wait gave up                        */
 #define LBS_EBUSY (-6)     /* resource busy (serving: queue full)           */
 #define LBS_ENOTFOUND (-7) /* unknown ticket                                */
+#define LBS_ECANCELED (-8) /* serving: the request was cancelled           */
 
 /* ---- enumerations ----------------------------------------------------- */
 /* storage precision of the distributions; u is kept at double precision or

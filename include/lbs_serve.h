@@ -123,6 +123,14 @@ int lbs_wait(lbs_server *s, uint64_t ticket, double timeout_s);
  * it stopped are still copied), LBS_EBUSY if it is not finished. */
 int lbs_result(lbs_server *s, uint64_t ticket, double *u, double *v, double *P);
 
+/* Cancel a ticket (no counterpart in the paper).  A queued request (also one
+ * swapped out by preemption) leaves the queue at once; a running one stops at
+ * the worker's next scheduling point, its fields as they stood then kept for
+ * lbs_result, and its device memory is released.  Either way the ticket ends
+ * failed with LBS_ECANCELED.  Cancelling a ticket that has already ended
+ * changes nothing.  Errors: LBS_ENOTFOUND. */
+int lbs_cancel(lbs_server *s, uint64_t ticket);
+
 /* Block until every submitted ticket is done or failed (timeout as lbs_wait). */
 int lbs_server_drain(lbs_server *s, double timeout_s);
 

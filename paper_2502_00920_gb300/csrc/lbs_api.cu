@@ -10,6 +10,7 @@
 
 #include "lbs_device.cuh"
 #include "lbs_internal.h"
+#include "lbs_trace.h"
 
 namespace lbs {
 
@@ -354,6 +355,7 @@ const char *lbs_strerror(int code) {
     case LBS_ETIMEOUT: return "timed out";
     case LBS_EBUSY: return "busy";
     case LBS_ENOTFOUND: return "not found";
+    case LBS_ECANCELED: return "cancelled";
     default: return "unknown error";
   }
 }
@@ -586,6 +588,7 @@ int lbs_set_initial(lbs_handle *h, const double *u0, const double *v0) {
 }
 
 int lbs_step(lbs_handle *h, int64_t n) {
+  const lbs::TraceRange trace("lbs_step");
   if (!h || n < 0) return fail(LBS_EINVAL, "bad step arguments");
   int rc = check_monitor(h, false);
   if (rc) return rc;

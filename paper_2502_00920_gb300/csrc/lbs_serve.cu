@@ -16,6 +16,7 @@
 #include "../../include/lbs_serve.h"
 #include "lbs_device.cuh"
 #include "lbs_internal.h"
+#include "lbs_trace.h"
 
 using lbs::BatchLattice;
 using lbs::BatchTile;
@@ -75,6 +76,7 @@ struct Req {
   size_t bytes = 0;
   lbs_handle *h = nullptr;
   std::vector<unsigned char> ckpt;  // state while swapped out (lbs_save)
+  bool cancel = false;              // lbs_cancel on a running request (under the server's lock)
   std::vector<double> u, v, P;
 };
 
@@ -220,6 +222,7 @@ struct ChunkGraph {
 
 cudaError_t run_chunk(lbs_server *s, const lbs::Launchers &L, int shape, int nres, int ni, int ne, int nl, int64_t n,
                       ChunkGraph &G) {
+  const lbs::TraceRange trace("lbs_server chunk");
   auto direct = [&]() -> cudaError_t {
     const cudaError_t e0 = lbs::launch_batch_edges(s->d_lats, nres, (int)n, s->stream);
     if (e0 != cudaSuccess) return e0;
@@ -301,6 +304,7 @@ void run(lbs_server *s) {
   auto complete = [&]() {
     if (!fl.on) return;
     fl.on = false;
+    std::vector<Req *> cancelled;
     cudaError_t e = fl.err;
     const cudaError_t es = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = es;
@@ -329,6 +333,8 @@ void run(lbs_server *s) {
       s->st.batch_tx = L.batch_shape(fl.shape).tx;
       s->st.batch_ty = L.batch_shape(fl.shape).ty;
       for (Req *r : res) r->k = std::min(r->k + fl.chunk, r->nsteps);
+      for (Req *r : res)
+        if (r->cancel) cancelled.push_back(r);
     }
     since_check += fl.chunk;
     const bool check = since_check >= kCheckEvery;
@@ -336,6 +342,8 @@ void run(lbs_server *s) {
     std::vector<Req *> keep;
     for (Req *r : res) {
       if (e != cudaSuccess) retire.emplace_back(r, LBS_ECUDA);
+      else if (std::find(cancelled.begin(), cancelled.end(), r) != cancelled.end())
+        retire.emplace_back(r, LBS_ECANCELED);
       else if (r->k >= r->nsteps) retire.emplace_back(r, LBS_OK);
       else if (check && unstable(r)) retire.emplace_back(r, LBS_EUNSTABLE);
       else keep.push_back(r);
@@ -666,6 +674,29 @@ int lbs_result(lbs_server *s, uint64_t ticket, double *u, double *v, double *P) 
   s->tickets.erase(it);
   delete r;
   return err;
+}
+
+int lbs_cancel(lbs_server *s, uint64_t ticket) {
+  if (!s) return LBS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->tickets.find(ticket);
+  if (it == s->tickets.end()) return LBS_ENOTFOUND;
+  Req *r = it->second;
+  if (r->state >= LBS_TICKET_DONE) return LBS_OK;
+  auto q = std::find(s->queue.begin(), s->queue.end(), r);
+  if (q != s->queue.end()) {  // not resident: it ends here
+    s->queue.erase(q);
+    r->ckpt.clear();
+    r->error = LBS_ECANCELED;
+    r->state = LBS_TICKET_FAILED;
+    r->t_done = s->now();
+    s->st.queued -= 1;
+    s->st.failed += 1;
+    s->cv_done.notify_all();
+    return LBS_OK;
+  }
+  r->cancel = true;  // resident (or being admitted): the worker stops it at its next scheduling point
+  return LBS_OK;
 }
 
 int lbs_server_drain(lbs_server *s, double timeout_s) {

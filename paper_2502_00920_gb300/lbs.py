@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "liblbs.so")
 _LOCK = threading.Lock()
 _LIB = None
 
-OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EBUSY, ENOTFOUND, ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7, -8
 PRECISION = {"fp64": 0, "fp32": 1, "fp16s": 2}
 MODEL = {"svk": 0, "nh": 1, "le": 2}
 KIND = {"periodic": 0, "dirichlet": 1, "neumann": 2}
@@ -144,6 +144,7 @@ SERVE_SIGNATURES = {
     "lbs_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double]),
     "lbs_result": (ctypes.c_int, [_vp, ctypes.c_uint64, _dp, _dp, _dp]),
     "lbs_server_drain": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "lbs_cancel": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "lbs_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
     "lbs_server_destroy": (ctypes.c_int, [_vp]),
 }
@@ -471,15 +472,23 @@ class Server:
         check(lib().lbs_wait(self._h, ctypes.c_uint64(ticket), float(timeout)))
 
     def result(self, ticket: int):
-        """(u, v, P, error code) of a finished ticket; forgets the ticket."""
+        """(u, v, P, error code) of a finished ticket (a failed one's fields as
+        they stood when it stopped, its code: EUNSTABLE, ECANCELED, ENOMEM ...);
+        forgets the ticket.  Raises for a ticket that is not finished or not
+        known."""
         case = self._cases.pop(ticket)
         ny, nx = case.ny, case.nx
         u, v, P = np.empty((ny, nx, 2)), np.empty((ny, nx, 2)), np.empty((ny, nx, 4))
         rc = lib().lbs_result(self._h, ctypes.c_uint64(ticket), _ptr(u), _ptr(v), _ptr(P))
-        if rc not in (OK, EUNSTABLE):
+        if rc in (EBUSY, ENOTFOUND, EINVAL):
             self._cases[ticket] = case
             check(rc)
         return u, v, P, rc
+
+    def cancel(self, ticket: int):
+        """Cancel a ticket: a queued one leaves the queue, a running one stops
+        at the next scheduling point; it ends failed with ECANCELED."""
+        check(lib().lbs_cancel(self._h, ticket))
 
     def drain(self, timeout: float = -1.0):
         check(lib().lbs_server_drain(self._h, float(timeout)))

@@ -130,6 +130,46 @@ def test_continuous_admission(L):
         assert np.array_equal(u, ua) and np.array_equal(v, va) and np.array_equal(P, Pa), case.name
 
 
+def test_cancel_queued_and_running_requests(L):
+    """lbs_cancel: a queued request leaves the queue at once, a running one
+    stops at the next scheduling point with its fields as they stood and its
+    memory released; both end failed with ECANCELED, and the request beside
+    them still equals its lattice run alone."""
+    long = I.tension(512, 256, 6500, ramp=500, model="nh", nu=0.2, peak=0.05, precision="fp32")
+    other = I.tension(64, 48, 200, ramp=50, model="svk", nu=0.1, precision="fp32")
+    fp = L.footprint(long)
+    # a budget that holds the long lattice and the small one, not a second long one
+    with L.Server(precision="fp32", chunk=32, hbm_budget=int(fp * 1.5)) as srv:
+        t_run = srv.submit(long)
+        t_wait = time.time()
+        while srv.poll(t_run)["iterations"] == 0 and time.time() - t_wait < 30:
+            time.sleep(0.001)
+        t_queued = srv.submit(long)  # does not fit beside the first: waits in the queue
+        t_other = srv.submit(other)
+        assert srv.poll(t_queued)["state"] == "queued"
+        srv.cancel(t_queued)
+        assert srv.poll(t_queued)["state"] == "failed"
+        srv.wait(t_other, 60)
+        srv.cancel(t_run)
+        srv.wait(t_run, 60)
+        info = srv.poll(t_run)
+        stats = srv.stats()
+        u, v, P, rc = srv.result(t_run)
+        uq, _, _, rcq = srv.result(t_queued)
+        uo, vo, Po, rco = srv.result(t_other)
+        with pytest.raises(L.LbsError) as e:
+            srv.cancel(t_run)  # collected: unknown now
+        assert e.value.code == L.ENOTFOUND
+    assert rc == L.ECANCELED and rcq == L.ECANCELED and rco == L.OK
+    assert 0 < info["iterations"] < long.nsteps and info["iterations"] % 32 == 0
+    assert stats["resident"] == 0 and stats["queued"] == 0
+    assert np.isfinite(u).all()
+    ua = alone(L, long.replace(nsteps=info["iterations"]))[0]
+    assert np.array_equal(u, ua)  # the fields where it stopped
+    ra = alone(L, other)
+    assert np.array_equal(uo, ra[0]) and np.array_equal(vo, ra[1]) and np.array_equal(Po, ra[2])
+
+
 def test_failures_reported_per_ticket(L):
     """A request that goes non-finite (linear material, nu = 0.45, loaded:
     beyond the scheme's stability) fails alone with LBS_EUNSTABLE; the
