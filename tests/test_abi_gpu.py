@@ -222,3 +222,24 @@ def test_separate_handles_on_separate_threads(L):
     assert not errors, errors
     for got, want in zip(out, ref):
         assert same(got, want)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
+def test_non_finite_initial_state_is_flagged_and_the_handle_stays_usable(L, precision):
+    """A NaN in the initial velocity (injected on the host, not on the GPU)
+    is reported as LBS_EUNSTABLE by the monitor at the first iteration it
+    runs after, the handle still answers lbs_fields, and a fresh handle of the
+    same lattice runs normally."""
+    c = case(precision)
+    v0 = np.zeros((c.ny, c.nx, 2))
+    v0[c.ny // 2, c.nx // 3, 0] = np.nan
+    with L.Simulation(c, monitor_interval=1) as s:
+        s.set_initial(None, v0)
+        with pytest.raises(L.LbsError) as e:
+            s.step(20)
+            s.sync()
+        assert e.value.code == L.EUNSTABLE
+        assert 0 <= s.unstable_iteration <= 2
+        u, v, P = s.fields()
+        assert not np.isfinite(v).all()
+    assert same(run(L, c, 40), run(L, c, 40))
