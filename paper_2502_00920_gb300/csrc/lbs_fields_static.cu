@@ -64,40 +64,18 @@ __global__ void __launch_bounds__(C::NT) fields_rows_kernel(const Params P, cons
   const int x0 = blockIdx.x * C::TX, y0 = (y_lo / C::TY + blockIdx.y) * C::TY;
   load_r2_from_state<C>(sm, P, u, x0, y0);
   __syncthreads();
-  phase_n<C, true>(sm, P, x0, y0, (R *)nullptr);
-  __syncthreads();
+  if (vo || Po) {
+    phase_n<C, true>(sm, P, x0, y0, (R *)nullptr);
+    __syncthreads();
+  }
   const size_t plane = (size_t)P.ny * P.pitch;
-  const R idx_ = (R)P.inv_dx, inv = gscale_inv<typename C::gs, R>(P), mu = (R)P.mu;
+  const double cr = P.c / P.rho0, hr = (0.5 * P.dt) / P.rho0;
   const int tx = threadIdx.x % C::TX, ty = threadIdx.x / C::TX;
   for (int i = 0; i < C::CPT; ++i) {
     const int lx = tx, ly = ty + i * C::NTY, x = x0 + lx, y = y0 + ly;
     if (x >= P.nx || y < y_lo || y >= y_hi) continue;
-    const size_t o = (size_t)(y - y_lo) * P.nx + x, idx = (size_t)y * P.pitch + x;
-    const double2 uv = u_value(sm.u[ly + 2][lx + 2]);
-    if (uo) {
-      uo[2 * o] = uv.x;
-      uo[2 * o + 1] = uv.y;
-    }
-    if (vo) {
-      R Sx, Sy;
-      Fd<C, true>::div(sm, P, lx + 1, ly + 1, x, y, idx_, (R)(P.rho0 * P.body[0]), (R)(P.rho0 * P.body[1]), Sx, Sy);
-      R gq[9], m1x, m1y;
-      for (int q = 1; q < 9; ++q) gq[q] = gload(g, q * plane + idx, inv);
-      first_moment(gq, m1x, m1y);
-      const double hdt = 0.5 * P.dt;
-      // g is held in units of g * 2^gshift (1 unless FP16 storage)
-      vo[2 * o] = (P.c * (double)(m1x * inv) - hdt * (double)Sx) / P.rho0;
-      vo[2 * o + 1] = (P.c * (double)(m1y * inv) - hdt * (double)Sy) / P.rho0;
-    }
-    if (Po) {
-      R H[4];
-      Fd<C, true>::grad(sm, P, lx + 1, ly + 1, x, y, idx_, H);
-      const R trH = H[0] + H[3];
-      Po[4 * o + 0] = (double)(sm.n[0][ly + 1][lx + 1] + mu * (R(2) * H[0] + trH));
-      Po[4 * o + 1] = (double)(sm.n[1][ly + 1][lx + 1] + mu * (H[1] + H[2]));
-      Po[4 * o + 2] = (double)(sm.n[2][ly + 1][lx + 1] + mu * (H[1] + H[2]));
-      Po[4 * o + 3] = (double)(sm.n[3][ly + 1][lx + 1] + mu * (R(2) * H[3] + trH));
-    }
+    node_fields<C>(sm, P, g, plane, (size_t)y * P.pitch + x, lx, ly, x, y, (size_t)(y - y_lo) * P.nx + x, cr, hr,
+                   uo, vo, Po);
   }
 }
 
