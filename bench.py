@@ -185,8 +185,10 @@ def run_reference(args, rank: int, world: int):
 
 def fp64_alu_roofline(mlups: float):
     """FP64 is bound by the FP64 pipe, not HBM: FLOP per node from the
-    committed ncu record (if taken on the current kernel source) against the
-    FP64 FMA rate of the GPU (2 per clock per SM); else None."""
+    committed ncu record (if taken on the current kernel source; DADD + DMUL +
+    2 DFMA as ncu counts them) against the FP64 FMA rate of the GPU (2 per
+    clock per SM), and the pipe operations per node against the pipe's slots;
+    else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "step_fp64_alu.json")) as f:
             rec = json.load(f)
@@ -194,8 +196,12 @@ def fp64_alu_roofline(mlups: float):
         if rec.get("source_hash") != B.source_hash():
             return None
         achieved = rec["flops_per_node"] * mlups * 1e6 / 1e12
+        # every DADD, DMUL and DFMA takes one slot of the pipe, which issues
+        # half the FMA-counted FLOP rate: the slots, not the FLOP, bound it
+        slots = rec["fp64_pipe_ops_per_node"] * mlups * 1e6 / (rec["peak_tflops"] * 1e12 / 2)
         return {"bound": "alu", "achieved": achieved, "peak": rec["peak_tflops"], "unit": "TFLOP/s",
                 "frac": achieved / rec["peak_tflops"], "flops_per_node": rec["flops_per_node"],
+                "fp64_pipe_ops_per_node": rec["fp64_pipe_ops_per_node"], "pipe_slot_frac": slots,
                 "fp64_pipe_active_ncu": rec["fp64_pipe_active"], "peak_source": rec["peak_source"]}
     except Exception:
         return None

@@ -406,13 +406,14 @@ __device__ void wall_rules(const Params &P, const R *bnd, const G *g, const doub
 // scale of g (the source arrives unscaled).
 template <class R>
 struct CollideK {
-  R mo, m6, m12, a1, a5, s9, s36;
+  R mo, m6, m9, m12, a1, a5, s9, s36;
 };
 template <class R>
 __device__ __forceinline__ CollideK<R> collide_k(R omega, R sigma, R scl) {
   const R ss = sigma * scl;
   return {-omega,
           -omega * (R(1) / R(6)),
+          -omega * (R(1) / R(9)),
           -omega * (R(1) / R(12)),
           omega * (R(1) / R(18)),
           -omega * (R(1) / R(36)),
@@ -420,8 +421,10 @@ __device__ __forceinline__ CollideK<R> collide_k(R omega, R sigma, R scl) {
           ss * (R(1) / R(36))};
 }
 
-// Each opposite pair takes the even relaxation A (same for both) and the odd
-// part b = -omega o + forcing with opposite signs: g = (f + A) +- b.
+// Each opposite pair takes the even relaxation A = Q a1 or Q a5 (the same for
+// both) and the odd part b = -omega o + forcing with opposite signs:
+// g = (f + A) +- b; in FP64 the product Q a is fused into the population's
+// own add, g = fma(Q, a, f) +- b.
 template <class R>
 __device__ __forceinline__ void collide(R f[9], R Sx, R Sy, const CollideK<R> &K) {
   const R s13 = f[1] + f[3], s24 = f[2] + f[4], s57 = f[5] + f[7], s68 = f[6] + f[8];
@@ -430,7 +433,7 @@ __device__ __forceinline__ void collide(R f[9], R Sx, R Sy, const CollideK<R> &K
   const R Q = fmr(R(4), s57 + s68, fmr(R(-2), s13 + s24, f[0]));
   const R fx = Sx * K.s9, fy = Sy * K.s9;
   const R f57 = (Sx + Sy) * K.s36, f68 = (Sy - Sx) * K.s36;
-  const R A1 = Q * K.a1, A5 = Q * K.a5;
+  const R A1 = Q * K.a1, A5 = Q * K.a5;  // (single precision; unused in FP64)
   R bx, by, b57, b68;
   if constexpr (sizeof(R) == 8) {
     // the odd parts, ox = (d13 - 2 (d57 - d68)) / 6 and so on, enter only as
@@ -455,15 +458,30 @@ __device__ __forceinline__ void collide(R f[9], R Sx, R Sy, const CollideK<R> &K
     b57 = fmr(K.mo, o57, f57);
     b68 = fmr(K.mo, o68, f68);
   }
-  f[0] = fmr(K.mo, Q * (R(1) / R(9)), f[0]);
-  f[1] = (f[1] + A1) + bx;
-  f[3] = (f[3] + A1) - bx;
-  f[2] = (f[2] + A1) + by;
-  f[4] = (f[4] + A1) - by;
-  f[5] = (f[5] + A5) + b57;
-  f[7] = (f[7] + A5) - b57;
-  f[6] = (f[6] + A5) + b68;
-  f[8] = (f[8] + A5) - b68;
+  if constexpr (sizeof(R) == 8) {
+    // three FP64 multiplies fewer per node
+    f[0] = fmr(Q, K.m9, f[0]);
+    f[1] = fmr(Q, K.a1, f[1]) + bx;
+    f[3] = fmr(Q, K.a1, f[3]) - bx;
+    f[2] = fmr(Q, K.a1, f[2]) + by;
+    f[4] = fmr(Q, K.a1, f[4]) - by;
+    f[5] = fmr(Q, K.a5, f[5]) + b57;
+    f[7] = fmr(Q, K.a5, f[7]) - b57;
+    f[6] = fmr(Q, K.a5, f[6]) + b68;
+    f[8] = fmr(Q, K.a5, f[8]) - b68;
+  } else {
+    // (single precision keeps the separate products: the fused form takes
+    // the FP16-storage TMA kernel past 64 registers)
+    f[0] = fmr(K.mo, Q * (R(1) / R(9)), f[0]);
+    f[1] = (f[1] + A1) + bx;
+    f[3] = (f[3] + A1) - bx;
+    f[2] = (f[2] + A1) + by;
+    f[4] = (f[4] + A1) - by;
+    f[5] = (f[5] + A5) + b57;
+    f[7] = (f[7] + A5) - b57;
+    f[6] = (f[6] + A5) + b68;
+    f[8] = (f[8] + A5) - b68;
+  }
 }
 
 // ------------------------------------------------------------------ tiles
